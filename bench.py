@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 coarse<->fine AMR transfer.
+
+Workload (the uniform batch): 2,048 hanging faces, coarse patches of 9^3
+volumes, overlap k = 3, U = 59 unknowns per volume (FP64, AoS), faces cycled
+over the six orientations, seeded smooth fields (4 Gaussians + 4 sinusoids per
+unknown, 1e-8 relative noise).  One step = Taylor-3 interpolation of all fine
+ghost volumes + Taylor-3 restriction of all coarse halo volumes.  The metric
+is ghost volume-unknowns per second (interpolated + restricted), with the
+interpolation kernel's achieved HBM bandwidth, the d-linear tensor-product
+path and Taylor-2 on the same GPU, and the error against the FP64 oracle.
+
+Rank 0 prints one JSON line.  Inputs (4.7 GB) are larger than L2 (129 MB),
+so no flush is needed between steps.  ``--impl reference`` times the CPU
+oracle instead (a bounded sample of the same workload, on the host cores).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+P, K, U, N_FACES = 9, 3, 59, 2048
+METRIC = "ghost volume-unknowns/s (Taylor-3 interpolation + restriction)"
+UNIT = "volume-unknowns/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["split", "fp64"], default="split")
+    ap.add_argument("--faces", type=int, default=N_FACES)
+    ap.add_argument("--no-extra", action="store_true", help="skip the d-linear / Taylor-2 / e2e / oracle legs")
+    return ap.parse_args()
+
+
+def dist_setup(n):
+    import torch
+    import torch.distributed as dist
+    if n > 1 or int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        rank = int(os.environ["RANK"])
+        local = int(os.environ.get("LOCAL_RANK", rank))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return dist, rank, dist.get_world_size(), local
+    return None, 0, 1, 0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.file.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def time_kernel(launch, n, stream):
+    """Average device time of one launch, CUDA events on the launching stream."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for a, b in evs:
+        a.record(stream)
+        launch()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / n
+
+
+def oracle_sample(items, coarse, fine, n_faces, U):
+    """A compact copy of the first n_faces items and their arrays on the host."""
+    import numpy as np
+    from paper_2504_15814_gb300 import workloads as wl
+    sub = items[:n_faces].copy()
+    arr = 2 * K * P * P * U
+    c = np.empty(n_faces * arr)
+    f = np.empty(n_faces * 9 * arr)
+    for i in range(n_faces):
+        co, fo = int(sub[i]["coarse_offset"]), int(sub[i]["fine_offset"])
+        c[i * arr:(i + 1) * arr] = coarse[co:co + arr].cpu().numpy()
+        f[i * 9 * arr:(i + 1) * 9 * arr] = fine[fo:fo + 9 * arr].cpu().numpy()
+        sub[i]["coarse_offset"] = i * arr
+        sub[i]["fine_offset"] = i * 9 * arr
+    return sub, c, f
+
+
+def time_oracle(sub, c, f, U, budget_s=10.0):
+    """Oracle interpolate + restrict on the sample; operators are built
+    before timing (construction happens once per plan on the GPU side too)."""
+    from oracle import transfer as tr
+    tr.restrict(sub[:6], U, f, c)
+    tr.interpolate(sub[:6], U, c, f)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        f2 = tr.interpolate(sub, U, c, f)
+        tr.restrict(sub, U, f2, c)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or reps >= 3:
+            break
+    per = el / reps
+    outs = len(sub) * (9 * K * P * P + K * P * P) * U
+    return outs / per, per
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, as it stands, on a bounded sample of the
+    workload, on this machine's host cores."""
+    import numpy as np
+    import torch
+    from paper_2504_15814_gb300 import workloads as wl
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    n_sample = 64
+    items, coarse, fine = wl.uniform_batch(n_faces=n_sample, p=P, k=K, U=U, order=3, config_index=1)
+    from oracle import transfer as tr
+    tr.interpolate(items[:6], U, coarse.numpy(), fine.numpy())
+    tr.restrict(items[:6], U, fine.numpy(), coarse.numpy())
+    times = []
+    c, f = coarse.numpy(), fine.numpy()
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        f2 = tr.interpolate(items, U, c, f)
+        tr.restrict(items, U, f2, c)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    per = sum(times) / len(times)
+    outs = n_sample * (9 * K * P * P + K * P * P) * U
+    value = outs / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"uniform batch sample: {n_sample} hanging faces of the 2048-face batch, "
+                                   f"p={P}, k={K}, U={U}, Taylor-3 interpolate+restrict",
+                       "faces": n_sample, "p": P, "k": K, "U": U},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n_sample} hanging faces per step (scipy CSR apply, single thread)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_2504_15814_gb300 import binding as B
+    from paper_2504_15814_gb300 import workloads as wl
+
+    dist, rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = B.PREC_SPLIT if args.precision == "split" else B.PREC_FP64
+    items, coarse, fine = wl.uniform_batch(n_faces=args.faces, p=P, k=K, U=U, order=3, config_index=1,
+                                           device=dev)
+    coarse_out = coarse.clone()
+    plan = B.Plan(items, U, coarse.numel(), fine.numel(), prec)
+    info = plan.info
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.interpolate(coarse, fine)
+        plan.restrict(fine, coarse_out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        # per-kernel durations for the roofline (same stream, same launches)
+        t_interp = time_kernel(lambda: plan.interpolate(coarse, fine), max(args.steps, 5), stream)
+        t_restrict = time_kernel(lambda: plan.restrict(fine, coarse_out), max(args.steps, 5), stream)
+    clocks = clk.summary()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    outs = (info["interp_outputs"] + info["restrict_outputs"]) * U
+    value = outs * world / (ms * 1e-3)
+
+    peaks, peak_src = measured_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    interp_gbs = info["interp_bytes"] / (t_interp * 1e-3) / 1e9
+    restrict_gbs = info["restrict_bytes"] / (t_restrict * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "interp_kernel", "achieved": interp_gbs, "peak": hbm_peak,
+                "unit": "GB/s", "frac": interp_gbs / hbm_peak, "traffic": None,
+                "algorithmic_bytes_per_launch": info["interp_bytes"], "launch_ms": t_interp,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                "restrict_kernel": {"achieved": restrict_gbs, "frac": restrict_gbs / hbm_peak,
+                                    "launch_ms": t_restrict, "algorithmic_bytes_per_launch": info["restrict_bytes"]}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == B.PREC_FP64 else "f64 base / f32 increment",
+            "data": "synthetic",
+            "config": {"workload": f"uniform batch: {args.faces} hanging faces per GPU, p={P}, k={K}, U={U}, "
+                                   f"FP64 AoS, Taylor-3 interpolate+restrict",
+                       "faces_per_gpu": args.faces, "p": P, "k": K, "U": U, "order": 3,
+                       "precision": args.precision, "parallelism": f"dp{world}" if world > 1 else "single GPU",
+                       "l2": "inputs (4.7 GB) larger than L2, no flush"},
+            "roofline": roofline, "clocks": clocks,
+            "gpu_launches": args.steps * (info["interp_launches"] + info["restrict_launches"])}
+
+    if rank == 0 and not args.no_extra:
+        line["compare"] = compare_paths(B, wl, items, coarse, fine, coarse_out, U, args, stream, plan)
+        line["e2e"] = e2e_leg(plan, coarse, fine, coarse_out, outs, args, stream)
+        line["err_vs_fp64"] = error_vs_oracle(items, coarse, fine, plan, U)
+        sub, c_h, f_h = oracle_sample(items, coarse, fine, 32, U)
+        v, per = time_oracle(sub, c_h, f_h, U)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "32 hanging faces of the batch, Taylor-3 interpolate+restrict, "
+                                          "operators prebuilt, scipy CSR apply (single thread)"}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def compare_paths(B, wl, items, coarse, fine, coarse_out, U, args, stream, plan_main):
+    """d-linear and Taylor-2 on the same workload and GPU, FP64 and split."""
+    out = {}
+    for name, order in (("dlinear", 1), ("taylor2", 2), ("taylor3", 3)):
+        for prec_name, prec in (("fp64", B.PREC_FP64), ("split", B.PREC_SPLIT)):
+            it = items.copy()
+            it["order"] = order
+            plan = B.Plan(it, U, coarse.numel(), fine.numel(), prec)
+            info = plan.info
+            step = lambda: (plan.interpolate(coarse, fine), plan.restrict(fine, coarse_out))
+            for _ in range(3):
+                step()
+            import torch
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n = max(5, args.steps // 2)
+            e0.record(stream)
+            for _ in range(n):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / n
+            ti = time_kernel(lambda: plan.interpolate(coarse, fine), n, stream)
+            tr_ = time_kernel(lambda: plan.restrict(fine, coarse_out), n, stream)
+            outs = (info["interp_outputs"] + info["restrict_outputs"]) * U
+            out[f"{name}_{prec_name}"] = {
+                "value": outs / (ms * 1e-3), "ms_per_step": ms, "interp_ms": ti, "restrict_ms": tr_,
+                "interp_gbs": info["interp_bytes"] / (ti * 1e-3) / 1e9,
+                "restrict_gbs": info["restrict_bytes"] / (tr_ * 1e-3) / 1e9,
+                "step_gbs": (info["interp_bytes"] + info["restrict_bytes"]) / (ms * 1e-3) / 1e9}
+            plan.close()
+    return out
+
+
+def e2e_leg(plan, coarse, fine, coarse_out, outs, args, stream):
+    """Same step through the C ABI with the inputs in pinned host memory:
+    H2D of both buffers, interpolate + restrict, D2H of both results."""
+    import torch
+    ch = torch.empty_like(coarse, device="cpu").pin_memory()
+    fh = torch.empty_like(fine, device="cpu").pin_memory()
+    ch.copy_(coarse)
+    fh.copy_(fine)
+    cho = torch.empty_like(ch).pin_memory()
+    fho = torch.empty_like(fh).pin_memory()
+    cd, fd, cod = torch.empty_like(coarse), torch.empty_like(fine), torch.empty_like(coarse)
+
+    def step():
+        cd.copy_(ch, non_blocking=True)
+        fd.copy_(fh, non_blocking=True)
+        cod.copy_(cd)
+        plan.interpolate(cd, fd)
+        plan.restrict(fd, cod)
+        fho.copy_(fd, non_blocking=True)
+        cho.copy_(cod, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    n = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    nbytes = (coarse.numel() + fine.numel()) * 8
+    return {"value": outs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes}
+
+
+def error_vs_oracle(items, coarse, fine, plan, U, n=400):
+    """Max and RMS normwise error of sampled outputs against the FP64 oracle."""
+    import numpy as np
+    import torch
+    from oracle import transfer as tr
+    f_out = fine.clone()
+    c_out = coarse.clone()
+    plan.interpolate(coarse, f_out)
+    plan.restrict(fine, c_out)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    arr = 2 * K * P * P * U
+    errs = []
+    chosen = rng.choice(len(items), 8, replace=False)
+    for i in chosen:
+        it = items[int(i)]
+        co, fo = int(it["coarse_offset"]), int(it["fine_offset"])
+        c_h = np.zeros(arr)
+        c_h[:] = coarse[co:co + arr].cpu().numpy()
+        f_h = fine[fo:fo + 9 * arr].cpu().numpy()
+        one = it.copy()
+        one["coarse_offset"], one["fine_offset"] = 0, 0
+        f_ref = tr.interpolate([one], U, c_h, f_h)
+        c_ref = tr.restrict([one], U, f_h, c_h)
+        fg = f_out[fo:fo + 9 * arr].cpu().numpy()
+        cg = c_out[co:co + arr].cpu().numpy()
+        for got, ref in ((fg, f_ref), (cg, c_ref)):
+            g = got.reshape(-1, U)
+            r = ref.reshape(-1, U)
+            errs.append((np.abs(g - r).max(axis=0) / np.maximum(np.abs(r).max(axis=0), 1e-300)))
+    e = np.concatenate(errs)
+    return {"max": float(e.max()), "rms": float(np.sqrt(np.mean(e ** 2))),
+            "sample": "8 random hanging faces, all outputs, normwise per (face, unknown)"}
+
+
+if __name__ == "__main__":
+    main()

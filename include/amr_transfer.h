@@ -1,0 +1,161 @@
+/*
+ * amr_transfer.h - C ABI of the GB300 coarse<->fine AMR transfer library.
+ *
+ * Operation (arXiv 2504.15814, Sec. 2): along a resolution transition of a
+ * three-partitioned, 2:1-balanced spacetree, a hanging face separates one
+ * coarse patch (p^3 volumes) from 3 x 3 fine patches.  The fine ghost
+ * volumes are interpolated from the coarse face data, Q^f = P Q^c, and the
+ * coarse halo volumes are restricted from the fine face data, Q^c = R Q^f.
+ * The higher-order operators (Sec. 3) reconstruct each output by a Taylor
+ * expansion of order 2 or 3 about the nearest input cell centre, with
+ * derivatives from finite-difference stencils over neighbouring centres; the
+ * d-linear operators are the tensor-product interpolation and averaging
+ * restriction of Sec. 2.  Every unknown of a volume uses the same operator
+ * (Sec. 2), so the library vectorises over the unknowns of the AoS layout.
+ *
+ * Data layout (Sec. 4.1: AoS, lexicographic):
+ *   A face array holds 2k layers along the face normal (k = overlap / halo
+ *   depth on each side) times p x p volumes, lexicographic with x fastest,
+ *   and the U unknowns of a volume contiguous (float64).  Face f in 0..5 has
+ *   normal axis f % 3; its tangential axes t0 < t1 are the other two.  For
+ *   f < 3 the coarse patch lies on the low side of the interface, for f >= 3
+ *   on the high side.  Normal index i sits at (i - k + 1/2) * spacing from the
+ *   interface.  Subface s = s0 + 3 s1 (s0 along t0, s1 along t1) is the fine
+ *   patch covering coarse tangential indices [s_t p/3, (s_t+1) p/3).
+ *
+ * Ownership: every data buffer is device memory owned by the caller; the
+ * plan owns its device tables.  All calls that take a stream are
+ * asynchronous on that stream (NULL = the legacy default stream); argument
+ * errors are detected on the host before anything is enqueued, and then
+ * nothing is enqueued.  A plan is bound to the device that was current when
+ * it was created and must be used from that device.  A plan may be used by
+ * one host thread at a time.
+ */
+#ifndef AMR_TRANSFER_H
+#define AMR_TRANSFER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMR_TRANSFER_ABI_VERSION 1
+
+typedef enum {
+  AMR_OK = 0,
+  AMR_ERR_INVALID_ARGUMENT = 1, /* null pointer, out-of-range field, overlapping outputs */
+  AMR_ERR_UNSUPPORTED = 2,      /* valid request this version cannot serve (see item rules) */
+  AMR_ERR_OUT_OF_MEMORY = 3,    /* a device or host allocation of the plan failed */
+  AMR_ERR_CUDA = 4,             /* a CUDA runtime call failed; the CUDA error is kept */
+  AMR_ERR_TIMEOUT = 5,          /* reserved: a bounded device-side wait gave up */
+  AMR_ERR_INTERNAL = 6
+} amr_status;
+
+typedef enum {
+  AMR_ORDER_DLINEAR = 1, /* Sec. 2: d-linear tensor-product interpolation / averaging restriction */
+  AMR_ORDER_TAYLOR2 = 2, /* Sec. 3: second-order Taylor, n = 10 coefficients */
+  AMR_ORDER_TAYLOR3 = 3  /* Sec. 3: third-order Taylor, n = 20 coefficients */
+} amr_order;
+
+typedef enum {
+  /* float64 arithmetic throughout; matches the float64 oracle to 1e-12 */
+  AMR_PREC_FP64 = 0,
+  /* float64 base value u_c and float64-accurate stencil differences
+     u_j - u_c; derivative and Taylor-increment arithmetic in float32 on those
+     differences; the increment is added back to the float64 base.  Results
+     are float64; the error bound is data dependent (see DESIGN) */
+  AMR_PREC_SPLIT = 1
+} amr_precision;
+
+/* One transfer item: one subface (one fine patch, a 1/9 block of P and R,
+ * Sec. 2) or a whole hanging face (all nine subfaces). */
+typedef struct {
+  int32_t face;          /* 0..5, see the layout note above */
+  int32_t subface;       /* 0..8 = s0 + 3 s1, or -1 for all nine subfaces */
+  int32_t patch_size;    /* p: a positive multiple of 3 (better alignment, Sec. 5.3), p <= 48 */
+  int32_t overlap;       /* k: 1..3; Taylor-m needs 2k >= m+1 and p >= m+1 */
+  int32_t order;         /* amr_order */
+  int32_t reserved;      /* must be 0 */
+  int64_t coarse_offset; /* element (float64) offset of the coarse face array, 2k p^2 U elements */
+  int64_t fine_offset;   /* element offset of the fine face array of the subface; for subface -1,
+                            nine consecutive fine face arrays in the order s = 0..8 */
+} amr_transfer_item;
+
+typedef struct {
+  int32_t abi_version;   /* AMR_TRANSFER_ABI_VERSION */
+  int32_t num_unknowns;  /* U >= 1: unknowns per volume (58 for first-order CCZ4, Sec. 2) */
+  int32_t precision;     /* amr_precision */
+  int32_t flags;         /* 0 (reserved) */
+  int64_t num_items;     /* >= 0 */
+  const amr_transfer_item* items; /* host array of num_items; copied at create */
+  int64_t coarse_elems;  /* float64 elements of the coarse buffer; every coarse face array must fit */
+  int64_t fine_elems;    /* float64 elements of the fine buffer; every fine face array must fit */
+} amr_transfer_desc;
+
+typedef struct amr_transfer_plan amr_transfer_plan; /* opaque, owned by the library */
+
+/* Validate the items, build the operator tables and the device work list
+ * (Sec. 3: operators are constructed once, off the time-step loop).
+ * Rules: fine face arrays of different items must not overlap; items that
+ * name the same coarse_offset must agree on face, p and k and own disjoint
+ * subfaces; coarse face arrays with different offsets must not overlap.
+ * Returns AMR_OK and *out, or an error and *out = NULL. */
+amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_plan** out);
+
+/* Q^f = P Q^c (Sec. 2): writes only the fine ghost halves (the k fine layers
+ * on the coarse side) of every item's fine face arrays.  coarse and fine are
+ * device pointers to coarse_elems / fine_elems float64 values; they must not
+ * overlap. */
+amr_status amr_transfer_plan_interpolate(amr_transfer_plan* plan, const double* coarse,
+                                         double* fine, void* cuda_stream);
+
+/* Q^c = R Q^f (Sec. 2, one call per subface in the paper's appendix "Code
+ * Overview"): writes only the coarse halo volumes (the k coarse layers on the
+ * fine side) that lie over each item's subfaces.  Reads both halves of the
+ * fine face arrays, the ghost half included. */
+amr_status amr_transfer_plan_restrict(amr_transfer_plan* plan, const double* fine,
+                                      double* coarse, void* cuda_stream);
+
+/* g_coarse = P^T g_fine over the whole coarse buffer: overwrites all
+ * coarse_elems values (zero where no weight reaches) and sums the
+ * contributions of items that share a coarse face array.  Only the ghost
+ * entries of g_fine are read.  Always float64. */
+amr_status amr_transfer_plan_interpolate_adjoint(amr_transfer_plan* plan, const double* g_fine,
+                                                 double* g_coarse, void* cuda_stream);
+
+/* g_fine = R^T g_coarse over the whole fine buffer: overwrites all
+ * fine_elems values (zero where no weight reaches).  Only the entries of
+ * g_coarse that restriction writes are read.  Always float64. */
+amr_status amr_transfer_plan_restrict_adjoint(amr_transfer_plan* plan, const double* g_coarse,
+                                              double* g_fine, void* cuda_stream);
+
+/* Plan facts used to report throughput. */
+typedef struct {
+  int64_t num_items;
+  int64_t interp_outputs;      /* fine ghost volumes written by interpolate */
+  int64_t restrict_outputs;    /* coarse halo volumes written by restrict */
+  int64_t interp_bytes;        /* algorithmic bytes of one interpolate: (volumes referenced by a
+                                  non-zero weight + volumes written) * U * 8 */
+  int64_t restrict_bytes;      /* the same for one restrict */
+  int32_t interp_launches;     /* kernels one interpolate call enqueues */
+  int32_t restrict_launches;   /* kernels one restrict call enqueues */
+} amr_transfer_plan_info;
+
+amr_status amr_transfer_plan_get_info(const amr_transfer_plan* plan, amr_transfer_plan_info* info);
+
+/* Release the plan's device tables (synchronises its device).  NULL is a no-op. */
+amr_status amr_transfer_plan_destroy(amr_transfer_plan* plan);
+
+/* Static text for a status code; never NULL. */
+const char* amr_status_string(amr_status status);
+
+/* Text of the last CUDA error seen by the calling thread in this library
+ * (after AMR_ERR_CUDA); never NULL. */
+const char* amr_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMR_TRANSFER_H */

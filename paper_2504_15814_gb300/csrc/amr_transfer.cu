@@ -1,0 +1,229 @@
+// C ABI of the transfer library: plan lifecycle and kernel launches.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "builder.hpp"
+#include "transfer_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_cuda_error = "no CUDA error";
+
+amr_status cuda_fail(cudaError_t e, const char* where) {
+  g_cuda_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return AMR_ERR_CUDA;
+}
+
+#define AMR_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+constexpr int kThreads = 256;
+constexpr int kSmemBudget = 48 * 1024;  // dynamic shared memory per interpolation CTA
+
+std::mutex g_tables_mutex;
+std::vector<int> g_tables_ready;  // per device
+
+amr_status upload_tables(int device) {
+  std::lock_guard<std::mutex> lock(g_tables_mutex);
+  if ((int)g_tables_ready.size() <= device) g_tables_ready.resize(device + 1, 0);
+  if (g_tables_ready[device]) return AMR_OK;
+  const amr::Tables& t = amr::tables();
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_wt_interp, t.wt_interp, sizeof t.wt_interp));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_wt_restrict, t.wt_restrict, sizeof t.wt_restrict));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_wt_interp_f, t.wt_interp_f, sizeof t.wt_interp_f));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_wt_restrict_f, t.wt_restrict_f, sizeof t.wt_restrict_f));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_ls, t.ls, sizeof t.ls));
+  g_tables_ready[device] = 1;
+  return AMR_OK;
+}
+
+template <typename T>
+amr_status upload(const std::vector<T>& h, T** d) {
+  *d = nullptr;
+  if (h.empty()) return AMR_OK;
+  cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(T));
+  if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return AMR_ERR_OUT_OF_MEMORY; }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  e = cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  return AMR_OK;
+}
+
+bool ranges_overlap(const void* a, int64_t abytes, const void* b, int64_t bbytes) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + bbytes && pb < pa + abytes;
+}
+
+}  // namespace
+
+struct amr_transfer_plan {
+  int device = 0;
+  int U = 0;
+  int precision = 0;
+  int64_t coarse_elems = 0, fine_elems = 0;
+  amr_transfer_item* items_d = nullptr;
+  amr::Tile* itiles_d = nullptr;
+  amr::Tile* rtiles_d = nullptr;
+  int n_itiles = 0, n_rtiles = 0;
+  int interp_smem = 0;
+  amr_transfer_plan_info info{};
+};
+
+static void free_plan(amr_transfer_plan* p) {
+  if (!p) return;
+  cudaFree(p->items_d);
+  cudaFree(p->itiles_d);
+  cudaFree(p->rtiles_d);
+  delete p;
+}
+
+extern "C" {
+
+const char* amr_status_string(amr_status s) {
+  switch (s) {
+    case AMR_OK: return "ok";
+    case AMR_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case AMR_ERR_UNSUPPORTED: return "unsupported";
+    case AMR_ERR_OUT_OF_MEMORY: return "out of memory";
+    case AMR_ERR_CUDA: return "CUDA error";
+    case AMR_ERR_TIMEOUT: return "timeout";
+    case AMR_ERR_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+const char* amr_last_cuda_error(void) { return g_cuda_error.c_str(); }
+
+amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_plan** out) {
+  if (!out) return AMR_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  if (!desc) return AMR_ERR_INVALID_ARGUMENT;
+  amr::BuildResult br;
+  try {
+    br = amr::build_plan(*desc, kSmemBudget);
+  } catch (const std::bad_alloc&) {
+    return AMR_ERR_OUT_OF_MEMORY;
+  }
+  if (br.status != AMR_OK) {
+    g_cuda_error = br.message;
+    return br.status;
+  }
+  if (br.interp_tiles.size() > (size_t)INT32_MAX || br.restrict_tiles.size() > (size_t)INT32_MAX)
+    return AMR_ERR_UNSUPPORTED;
+  int device = 0;
+  AMR_CUDA(cudaGetDevice(&device));
+  amr_status st = upload_tables(device);
+  if (st != AMR_OK) return st;
+
+  amr_transfer_plan* p = new (std::nothrow) amr_transfer_plan;
+  if (!p) return AMR_ERR_OUT_OF_MEMORY;
+  p->device = device;
+  p->U = desc->num_unknowns;
+  p->precision = desc->precision;
+  p->coarse_elems = desc->coarse_elems;
+  p->fine_elems = desc->fine_elems;
+  std::vector<amr_transfer_item> items(desc->items, desc->items + desc->num_items);
+  if ((st = upload(items, &p->items_d)) != AMR_OK ||
+      (st = upload(br.interp_tiles, &p->itiles_d)) != AMR_OK ||
+      (st = upload(br.restrict_tiles, &p->rtiles_d)) != AMR_OK) {
+    free_plan(p);
+    return st;
+  }
+  p->n_itiles = (int)br.interp_tiles.size();
+  p->n_rtiles = (int)br.restrict_tiles.size();
+  p->interp_smem = br.max_interp_smem;
+  if (p->interp_smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(amr::interp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(amr::interp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
+    if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaFuncSetAttribute"); }
+  }
+  p->info.num_items = desc->num_items;
+  p->info.interp_outputs = br.interp_outputs;
+  p->info.restrict_outputs = br.restrict_outputs;
+  p->info.interp_bytes = br.interp_bytes;
+  p->info.restrict_bytes = br.restrict_bytes;
+  p->info.interp_launches = p->n_itiles > 0 ? 1 : 0;
+  p->info.restrict_launches = p->n_rtiles > 0 ? 1 : 0;
+  *out = p;
+  return AMR_OK;
+}
+
+static amr_status check_call(const amr_transfer_plan* p, const void* in, int64_t in_elems, const void* out,
+                             int64_t out_elems) {
+  if (!p) return AMR_ERR_INVALID_ARGUMENT;
+  if ((in_elems > 0 && !in) || (out_elems > 0 && !out)) return AMR_ERR_INVALID_ARGUMENT;
+  if (in && out && ranges_overlap(in, in_elems * 8, out, out_elems * 8)) return AMR_ERR_INVALID_ARGUMENT;
+  int dev = -1;
+  AMR_CUDA(cudaGetDevice(&dev));
+  if (dev != p->device) return AMR_ERR_INVALID_ARGUMENT;
+  return AMR_OK;
+}
+
+amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coarse, double* fine, void* stream) {
+  amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, fine, p ? p->fine_elems : 0);
+  if (st != AMR_OK) return st;
+  if (p->n_itiles == 0) return AMR_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->precision == AMR_PREC_SPLIT)
+    amr::interp_kernel<true><<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
+  else
+    amr::interp_kernel<false><<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
+  AMR_CUDA(cudaGetLastError());
+  return AMR_OK;
+}
+
+amr_status amr_transfer_plan_restrict(amr_transfer_plan* p, const double* fine, double* coarse, void* stream) {
+  amr_status st = check_call(p, fine, p ? p->fine_elems : 0, coarse, p ? p->coarse_elems : 0);
+  if (st != AMR_OK) return st;
+  if (p->n_rtiles == 0) return AMR_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->precision == AMR_PREC_SPLIT)
+    amr::restrict_kernel<true><<<p->n_rtiles, kThreads, 0, s>>>(p->items_d, p->rtiles_d, p->U, fine, coarse);
+  else
+    amr::restrict_kernel<false><<<p->n_rtiles, kThreads, 0, s>>>(p->items_d, p->rtiles_d, p->U, fine, coarse);
+  AMR_CUDA(cudaGetLastError());
+  return AMR_OK;
+}
+
+amr_status amr_transfer_plan_interpolate_adjoint(amr_transfer_plan* p, const double* g_fine, double* g_coarse,
+                                                 void* stream) {
+  (void)p; (void)g_fine; (void)g_coarse; (void)stream;
+  return AMR_ERR_UNSUPPORTED;
+}
+
+amr_status amr_transfer_plan_restrict_adjoint(amr_transfer_plan* p, const double* g_coarse, double* g_fine,
+                                              void* stream) {
+  (void)p; (void)g_coarse; (void)g_fine; (void)stream;
+  return AMR_ERR_UNSUPPORTED;
+}
+
+amr_status amr_transfer_plan_get_info(const amr_transfer_plan* p, amr_transfer_plan_info* info) {
+  if (!p || !info) return AMR_ERR_INVALID_ARGUMENT;
+  *info = p->info;
+  return AMR_OK;
+}
+
+amr_status amr_transfer_plan_destroy(amr_transfer_plan* p) {
+  if (!p) return AMR_OK;
+  const int dev = p->device;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != dev) cudaSetDevice(dev);
+  cudaDeviceSynchronize();
+  free_plan(p);
+  if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+  return AMR_OK;
+}
+
+}  // extern "C"

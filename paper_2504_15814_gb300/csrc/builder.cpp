@@ -1,0 +1,295 @@
+// Host-side operator builder: weight tables, validation, tiling, byte counts.
+#include "builder.hpp"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <numeric>
+
+namespace amr {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Exact rational arithmetic for the 1-D weights (small windows: numerators and
+// denominators stay far inside int64).
+// ---------------------------------------------------------------------------
+struct Q {
+  int64_t n = 0, d = 1;
+  Q() = default;
+  Q(int64_t num, int64_t den = 1) : n(num), d(den) { norm(); }
+  void norm() {
+    if (d < 0) { n = -n; d = -d; }
+    int64_t g = std::gcd(n < 0 ? -n : n, d);
+    if (g > 1) { n /= g; d /= g; }
+  }
+  double to_double() const { return (double)n / (double)d; }
+};
+Q operator+(Q a, Q b) { return Q(a.n * b.d + b.n * a.d, a.d * b.d); }
+Q operator-(Q a, Q b) { return Q(a.n * b.d - b.n * a.d, a.d * b.d); }
+Q operator*(Q a, Q b) { return Q(a.n * b.n, a.d * b.d); }
+Q operator/(Q a, Q b) { return Q(a.n * b.d, a.d * b.n); }
+
+// Coefficient of t^r of the Lagrange basis polynomial l_i(t) on the points
+// x_j = j - pos (j = 0..L-1), t measured from the expansion point: equals
+// (d^r l_i / dt^r)(0) / r!, i.e. the Taylor coefficient the weight feeds.
+Q lagrange_taylor_coeff(int L, int pos, int r, int i) {
+  std::vector<Q> poly{Q(1)};
+  Q denom(1);
+  const int xi = i - pos;
+  for (int j = 0; j < L; ++j) {
+    if (j == i) continue;
+    const int xj = j - pos;
+    std::vector<Q> next(poly.size() + 1, Q(0));
+    for (size_t q = 0; q < poly.size(); ++q) {  // poly * (t - xj)
+      next[q + 1] = next[q + 1] + poly[q];
+      next[q] = next[q] - poly[q] * Q(xj);
+    }
+    poly.swap(next);
+    denom = denom * Q(xi - xj);
+  }
+  if (r >= (int)poly.size()) return Q(0);
+  return poly[r] / denom;
+}
+
+Tables make_tables() {
+  Tables t{};
+  for (int L = 3; L <= 5; ++L)
+    for (int pos = 0; pos < L; ++pos)
+      for (int r = 1; r <= 3; ++r) {
+        Q scale(1);
+        for (int q = 0; q < r; ++q) scale = scale * Q(1, 3);
+        for (int i = 0; i < L; ++i) {
+          const Q c = lagrange_taylor_coeff(L, pos, r, i);
+          const int idx = wt_offset(L) + (pos * 3 + r - 1) * L + i;
+          t.wt_restrict[idx] = c.to_double();
+          t.wt_interp[idx] = (c * scale).to_double();
+          t.wt_restrict_f[idx] = (float)t.wt_restrict[idx];
+          t.wt_interp_f[idx] = (float)t.wt_interp[idx];
+        }
+      }
+  // Least-squares line through the fine patch's own layers (centres at
+  // (i + 1/2)/3 H), evaluated at coarse halo layer j (centre (j + 1/2) H).
+  for (int k = 1; k <= 3; ++k) {
+    std::vector<int> layers;
+    if (k == 1) layers = {-1, 0};
+    else for (int i = 0; i < k; ++i) layers.push_back(i);
+    const int nl = (int)layers.size();
+    Q mean(0);
+    for (int i : layers) mean = mean + Q(2 * i + 1, 6);
+    mean = mean / Q(nl);
+    Q sxx(0);
+    for (int i : layers) { Q dx = Q(2 * i + 1, 6) - mean; sxx = sxx + dx * dx; }
+    for (int j = 0; j < k; ++j) {
+      const Q xc(2 * j + 1, 2);
+      for (int s = 0; s < nl; ++s) {
+        const Q w = Q(1, nl) + (Q(2 * layers[s] + 1, 6) - mean) * (xc - mean) / sxx;
+        t.ls[ls_index(k, j, s)] = w.to_double();
+        t.ls_f[ls_index(k, j, s)] = (float)w.to_double();
+      }
+    }
+  }
+  return t;
+}
+
+bool overlaps(int64_t a0, int64_t a1, int64_t b0, int64_t b1) { return a0 < b1 && b0 < a1; }
+
+// Mark the volumes one interpolation centre references; reference volume index
+// (j + k) * p * p + b * p + a.
+void mark_interp(std::vector<char>& m, int p, int k, int order, int a, int b) {
+  auto mark = [&](int j, int aa, int bb) { m[((size_t)(j + k) * p + bb) * p + aa] = 1; };
+  if (order == AMR_ORDER_DLINEAR) {
+    const int jlo = k >= 3 ? -2 : -1;
+    const int alo = (a == 0) ? 0 : a - 1, ahi = (a == p - 1) ? p - 1 : a + 1;
+    const int blo = (b == 0) ? 0 : b - 1, bhi = (b == p - 1) ? p - 1 : b + 1;
+    for (int j = jlo; j <= 0; ++j) {
+      for (int bb = blo; bb <= bhi; ++bb)
+        for (int aa = alo; aa <= ahi; ++aa) mark(j, aa, bb);
+    }
+    return;
+  }
+  int s, l;
+  const int c[3] = {-1, a, b};
+  const int lo[3] = {-k, 0, 0}, hi[3] = {k - 1, p - 1, p - 1};
+  for (int d = 0; d < 3; ++d) {  // pure derivatives: lines through the centre
+    stencil_window(c[d], lo[d], hi[d], pure_exactness(order), s, l);
+    for (int q = s; q < s + l; ++q) {
+      int x[3] = {c[0], c[1], c[2]};
+      x[d] = q;
+      mark(x[0], x[1], x[2]);
+    }
+  }
+  int ms[3], ml[3];
+  for (int d = 0; d < 3; ++d) stencil_window(c[d], lo[d], hi[d], mixed_exactness(order), ms[d], ml[d]);
+  for (int d = 0; d < 3; ++d)
+    for (int e = d + 1; e < 3; ++e)  // mixed pairs: planes
+      for (int qd = ms[d]; qd < ms[d] + ml[d]; ++qd)
+        for (int qe = ms[e]; qe < ms[e] + ml[e]; ++qe) {
+          int x[3] = {c[0], c[1], c[2]};
+          x[d] = qd;
+          x[e] = qe;
+          mark(x[0], x[1], x[2]);
+        }
+  if (order == 3)  // u_{t0 t1 n}: the box
+    for (int q0 = ms[0]; q0 < ms[0] + ml[0]; ++q0)
+      for (int q1 = ms[1]; q1 < ms[1] + ml[1]; ++q1)
+        for (int q2 = ms[2]; q2 < ms[2] + ml[2]; ++q2) mark(q0, q1, q2);
+}
+
+// Fine volumes one restriction column references (reference frame of the
+// subface's fine array, local tangential q0, q1 of the coincident column).
+void mark_restrict(std::vector<char>& m, int p, int k, int order, int q0, int q1) {
+  auto mark = [&](int i, int aa, int bb) { m[((size_t)(i + k) * p + bb) * p + aa] = 1; };
+  if (order == AMR_ORDER_DLINEAR) {
+    const int ilo = (k == 1) ? -1 : 0, ihi = (k == 1) ? 0 : k - 1;
+    for (int i = ilo; i <= ihi; ++i)
+      for (int db = -1; db <= 1; ++db)
+        for (int da = -1; da <= 1; ++da) mark(i, q0 + da, q1 + db);
+    return;
+  }
+  if (k >= 2) mark(1, q0, q1);  // injection
+  if (k >= 2 && k - 1 >= 1) {
+    int s, l;
+    stencil_window(k - 1, -k, k - 1, pure_exactness(order), s, l);
+    for (int i = s; i < s + l; ++i) mark(i, q0, q1);
+  }
+}
+
+}  // namespace
+
+const Tables& tables() {
+  static const Tables t = make_tables();
+  return t;
+}
+
+static BuildResult fail(amr_status st, const std::string& msg) {
+  BuildResult r;
+  r.status = st;
+  r.message = msg;
+  return r;
+}
+
+BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
+  if (desc.abi_version != AMR_TRANSFER_ABI_VERSION)
+    return fail(AMR_ERR_INVALID_ARGUMENT, "abi_version mismatch");
+  if (desc.num_unknowns < 1) return fail(AMR_ERR_INVALID_ARGUMENT, "num_unknowns must be >= 1");
+  if (desc.num_unknowns > 32767) return fail(AMR_ERR_UNSUPPORTED, "num_unknowns > 32767");
+  if (desc.precision != AMR_PREC_FP64 && desc.precision != AMR_PREC_SPLIT)
+    return fail(AMR_ERR_INVALID_ARGUMENT, "unknown precision");
+  if (desc.flags != 0) return fail(AMR_ERR_INVALID_ARGUMENT, "flags must be 0");
+  if (desc.num_items < 0 || (desc.num_items > 0 && desc.items == nullptr))
+    return fail(AMR_ERR_INVALID_ARGUMENT, "bad item list");
+  if (desc.num_items > (int64_t)1 << 30) return fail(AMR_ERR_UNSUPPORTED, "too many items");
+  if (desc.coarse_elems < 0 || desc.fine_elems < 0) return fail(AMR_ERR_INVALID_ARGUMENT, "negative buffer size");
+
+  const int64_t U = desc.num_unknowns;
+  BuildResult r;
+  struct Interval { int64_t lo, hi; int64_t item; };
+  std::vector<Interval> fine_iv;
+  std::map<int64_t, std::vector<int64_t>> coarse_groups;
+
+  for (int64_t it = 0; it < desc.num_items; ++it) {
+    const amr_transfer_item& x = desc.items[it];
+    char buf[160];
+    auto bad = [&](amr_status st, const char* what) {
+      std::snprintf(buf, sizeof buf, "item %lld: %s", (long long)it, what);
+      return fail(st, buf);
+    };
+    if (x.face < 0 || x.face > 5) return bad(AMR_ERR_INVALID_ARGUMENT, "face not in 0..5");
+    if (x.subface < -1 || x.subface > 8) return bad(AMR_ERR_INVALID_ARGUMENT, "subface not in -1..8");
+    if (x.order < 1 || x.order > 3) return bad(AMR_ERR_INVALID_ARGUMENT, "order not in 1..3");
+    if (x.reserved != 0) return bad(AMR_ERR_INVALID_ARGUMENT, "reserved must be 0");
+    if (x.patch_size < 1 || x.overlap < 1) return bad(AMR_ERR_INVALID_ARGUMENT, "p and k must be positive");
+    if (x.overlap > x.patch_size) return bad(AMR_ERR_INVALID_ARGUMENT, "k > p");
+    if (x.patch_size % 3 != 0) return bad(AMR_ERR_UNSUPPORTED, "p must be a multiple of 3");
+    if (x.patch_size > 48) return bad(AMR_ERR_UNSUPPORTED, "p > 48");
+    if (x.overlap > 3) return bad(AMR_ERR_UNSUPPORTED, "k > 3");
+    if (x.order >= 2 && (2 * x.overlap < x.order + 1 || x.patch_size < x.order + 1))
+      return bad(AMR_ERR_UNSUPPORTED, "Taylor order needs 2k >= m+1 and p >= m+1");
+    if (x.coarse_offset < 0 || x.fine_offset < 0) return bad(AMR_ERR_INVALID_ARGUMENT, "negative offset");
+    const int64_t arr = 2LL * x.overlap * x.patch_size * x.patch_size * U;
+    const int64_t nsub = x.subface < 0 ? 9 : 1;
+    if (x.coarse_offset > desc.coarse_elems - arr) return bad(AMR_ERR_INVALID_ARGUMENT, "coarse face array out of range");
+    if (x.fine_offset > desc.fine_elems - nsub * arr) return bad(AMR_ERR_INVALID_ARGUMENT, "fine face arrays out of range");
+    fine_iv.push_back({x.fine_offset, x.fine_offset + nsub * arr, it});
+    coarse_groups[x.coarse_offset].push_back(it);
+  }
+  std::sort(fine_iv.begin(), fine_iv.end(), [](const Interval& a, const Interval& b) { return a.lo < b.lo; });
+  for (size_t i = 1; i < fine_iv.size(); ++i)
+    if (fine_iv[i].lo < fine_iv[i - 1].hi) return fail(AMR_ERR_INVALID_ARGUMENT, "fine face arrays of two items overlap");
+  int64_t prev_hi = INT64_MIN;
+  for (auto& [off, members] : coarse_groups) {
+    const amr_transfer_item& f = desc.items[members[0]];
+    int used = 0;
+    for (int64_t m : members) {
+      const amr_transfer_item& x = desc.items[m];
+      if (x.face != f.face || x.patch_size != f.patch_size || x.overlap != f.overlap)
+        return fail(AMR_ERR_INVALID_ARGUMENT, "items sharing a coarse face array disagree on face, p or k");
+      const int mask = x.subface < 0 ? 0x1ff : (1 << x.subface);
+      if (used & mask) return fail(AMR_ERR_INVALID_ARGUMENT, "items sharing a coarse face array restrict the same subface");
+      used |= mask;
+    }
+    if (off < prev_hi) return fail(AMR_ERR_INVALID_ARGUMENT, "coarse face arrays overlap");
+    prev_hi = off + 2LL * f.overlap * f.patch_size * f.patch_size * U;
+  }
+
+  // Tiles and byte counts.
+  const int TMAX = 8;
+  std::map<std::tuple<int, int, int, int>, std::pair<int64_t, int64_t>> ref_cache;  // (p,k,order,sub) -> (interp refs, restrict refs)
+  for (int64_t it = 0; it < desc.num_items; ++it) {
+    const amr_transfer_item& x = desc.items[it];
+    const int p = x.patch_size, k = x.overlap, m = x.order, w = p / 3;
+    std::vector<char> cmark((size_t)2 * k * p * p, 0);
+    for (int sl = 0; sl < (x.subface < 0 ? 9 : 1); ++sl) {
+      const int sub = x.subface < 0 ? sl : x.subface;
+      const int s0 = sub % 3, s1 = sub / 3;
+      for (int a0 = s0 * w; a0 < (s0 + 1) * w; a0 += TMAX)
+        for (int b0 = s1 * w; b0 < (s1 + 1) * w; b0 += TMAX) {
+          const int na = std::min(TMAX, (s0 + 1) * w - a0), nb = std::min(TMAX, (s1 + 1) * w - b0);
+          // interpolation region -> unknown chunk from the shared-memory budget
+          IRange rn, ra, rb;
+          interp_region(p, k, m, a0, na, b0, nb, rn, ra, rb);
+          const int64_t vols = (int64_t)(rn.hi - rn.lo + 1) * (ra.hi - ra.lo + 1) * (rb.hi - rb.lo + 1);
+          int nu_max = (int)std::min<int64_t>(U, std::max<int64_t>(1, smem_budget / (vols * 8)));
+          const int nchunks = (int)((U + nu_max - 1) / nu_max);
+          const int nu = (int)((U + nchunks - 1) / nchunks);
+          for (int c = 0; c < nchunks; ++c) {
+            Tile t{};
+            t.item = (int32_t)it; t.sub = (int8_t)sub; t.slot = (int8_t)(x.subface < 0 ? sub : 0);
+            t.na = (int8_t)na; t.nb = (int8_t)nb; t.a0 = (int16_t)a0; t.b0 = (int16_t)b0;
+            t.u0 = (int16_t)(c * nu); t.nu = (int16_t)std::min<int64_t>(nu, U - c * nu);
+            r.interp_tiles.push_back(t);
+            r.max_interp_smem = std::max<int>(r.max_interp_smem, (int)(vols * t.nu * 8));
+          }
+          Tile t{};
+          t.item = (int32_t)it; t.sub = (int8_t)sub; t.slot = (int8_t)(x.subface < 0 ? sub : 0);
+          t.na = (int8_t)na; t.nb = (int8_t)nb; t.a0 = (int16_t)a0; t.b0 = (int16_t)b0;
+          for (int64_t u0 = 0; u0 < U; u0 += 128) {
+            t.u0 = (int16_t)u0; t.nu = (int16_t)std::min<int64_t>(128, U - u0);
+            r.restrict_tiles.push_back(t);
+          }
+        }
+      for (int b = s1 * w; b < (s1 + 1) * w; ++b)
+        for (int a = s0 * w; a < (s0 + 1) * w; ++a) mark_interp(cmark, p, k, m, a, b);
+      // restriction references (per subface fine array)
+      auto key = std::make_tuple(p, k, m, sub);
+      auto f = ref_cache.find(key);
+      if (f == ref_cache.end()) {
+        std::vector<char> fmark((size_t)2 * k * p * p, 0);
+        for (int b = s1 * w; b < (s1 + 1) * w; ++b)
+          for (int a = s0 * w; a < (s0 + 1) * w; ++a) mark_restrict(fmark, p, k, m, 3 * a + 1 - s0 * p, 3 * b + 1 - s1 * p);
+        int64_t cnt = std::count(fmark.begin(), fmark.end(), 1);
+        f = ref_cache.emplace(key, std::make_pair((int64_t)0, cnt)).first;
+      }
+      r.restrict_bytes += f->second.second * U * 8;
+      r.interp_outputs += (int64_t)k * p * p;
+      r.restrict_outputs += (int64_t)k * w * w;
+    }
+    r.interp_bytes += (int64_t)std::count(cmark.begin(), cmark.end(), 1) * U * 8;
+  }
+  r.interp_bytes += r.interp_outputs * U * 8;
+  r.restrict_bytes += r.restrict_outputs * U * 8;
+  return r;
+}
+
+}  // namespace amr

@@ -1,0 +1,185 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs, element by element.
+
+FP64 path: normwise relative error per (item, unknown) <= 1e-12.
+Split path: the float32 derivative/increment arithmetic on float64
+differences gives an error below SPLIT_BOUND on the smooth synthetic fields
+(derived bound: a few float32 roundings of the increment, ~1e-7 of it, and the
+increment is at most the field's variation over one coarse cell)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import transfer as tr
+from paper_2504_15814_gb300 import binding as B
+from paper_2504_15814_gb300 import workloads as wl
+
+from .parity import gpu_interpolate, gpu_restrict, normwise_errors, record, written_masks
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+SPLIT_BOUND = 2e-6
+
+
+def _batch(faces, subs, ps, ks, orders, U, seed=0):
+    items, cl, fl = wl.make_items(faces, subs, ps, ks, orders, U)
+    rng = np.random.Generator(np.random.PCG64(wl.SEED_BASE + 100 + seed))
+    field = wl.SmoothField(U, rng)
+    coarse, fine = wl.sample_buffers(items, U, cl, fl, field, wl.origins_in_box(len(items), rng))
+    wl.add_noise(coarse, 1e-8, rng)
+    wl.add_noise(fine, 1e-8, rng)
+    return items, coarse.numpy(), fine.numpy()
+
+
+def _check(items, U, coarse, fine, precision, tol):
+    fmask, cmask = written_masks(items, U, len(coarse), len(fine))
+    plan = B.Plan(items, U, len(coarse), len(fine), precision)
+    f_ref = tr.interpolate(items, U, coarse, fine)
+    f_gpu = gpu_interpolate(plan, coarse, fine)
+    # entries interpolate must not touch are bit-identical
+    assert np.array_equal(f_gpu[~fmask], fine[~fmask])
+    e_i, rms_i = normwise_errors(items, U, f_gpu, f_ref, fmask, "fine")
+    c_ref = tr.restrict(items, U, fine, coarse)
+    c_gpu = gpu_restrict(plan, fine, coarse)
+    assert np.array_equal(c_gpu[~cmask], coarse[~cmask])
+    e_r, rms_r = normwise_errors(items, U, c_gpu, c_ref, cmask, "coarse")
+    record(test=_check.__name__, orders=sorted({int(o) for o in items["order"]}), precision=precision,
+           n_items=len(items), U=U, interp_max=e_i, interp_rms=rms_i, restrict_max=e_r, restrict_rms=rms_r)
+    assert e_i <= tol, (e_i, rms_i)
+    assert e_r <= tol, (e_r, rms_r)
+    plan.close()
+    return e_i, e_r
+
+
+@pytest.mark.parametrize("precision,tol", [(B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND)])
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_whole_faces_all_orientations(order, precision, tol):
+    # 12 hanging faces, all six orientations twice, p = 9, k = 3, U = 59
+    # (unknowns split into ragged chunks)
+    n = 12
+    items, c, f = _batch([i % 6 for i in range(n)], [-1] * n, [9] * n, [3] * n, [order] * n, 59, seed=order)
+    _check(items, 59, c, f, precision, tol)
+
+
+@pytest.mark.parametrize("precision,tol", [(B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND)])
+@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("p,k", [(6, 2), (6, 3), (12, 2), (12, 3)])
+def test_subface_items(order, p, k, precision, tol):
+    faces = [f for f in range(6) for _ in range(9)]
+    subs = [s for _ in range(6) for s in range(9)]
+    n = len(faces)
+    items, c, f = _batch(faces, subs, [p] * n, [k] * n, [order] * n, 7, seed=10 * p + k)
+    _check(items, 7, c, f, precision, tol)
+
+
+def test_dlinear_overlap_one():
+    n = 6
+    items, c, f = _batch(list(range(6)), [-1] * n, [6] * n, [1] * n, [1] * n, 3, seed=5)
+    _check(items, 3, c, f, B.PREC_FP64, FP64_TOL)
+
+
+def test_mixed_batch_and_large_patches():
+    # uneven batch: p in {6, 9, 12, 24, 48}, k in {2, 3}, orders mixed, U = 5
+    rng = np.random.default_rng(3)
+    n = 40
+    ps = rng.choice([6, 9, 12, 24, 48], n)
+    ks = rng.choice([2, 3], n)
+    orders = rng.choice([1, 2, 3], n)
+    faces = rng.integers(0, 6, n)
+    subs = rng.integers(-1, 9, n)
+    items, c, f = _batch(faces, subs, ps, ks, orders, 5, seed=7)
+    _check(items, 5, c, f, B.PREC_FP64, FP64_TOL)
+
+
+def test_single_face_quadratic_exact():
+    """One coarse face p = 6, k = 3, U = 1, Taylor-2, random quadratic with
+    coefficients U[-1,1] sampled on the unit cube: reproduced to rounding."""
+    items, cl, fl = wl.make_items([0], [-1], [6], [3], [2], 1)
+    rng = np.random.Generator(np.random.PCG64(wl.SEED_BASE + 0))
+    coef = rng.uniform(-1, 1, 10)
+    H = 1.0 / 6
+
+    def quad(x):
+        x = x * H
+        t = [torch.ones_like(x[:, 0]), x[:, 0], x[:, 1], x[:, 2], x[:, 0] ** 2, x[:, 1] ** 2, x[:, 2] ** 2,
+             x[:, 0] * x[:, 1], x[:, 0] * x[:, 2], x[:, 1] * x[:, 2]]
+        return sum(c * v for c, v in zip(coef, t))[:, None]
+
+    coarse, fine = wl.polynomial_buffers(items, 1, cl, fl, quad, origins=np.array([[1.0 / H, 0.0, 0.0]]))
+    c, f = coarse.numpy(), fine.numpy()
+    plan = B.Plan(items, 1, cl, fl, B.PREC_FP64)
+    f_gpu = gpu_interpolate(plan, c, f)
+    # the quadratic itself is the exact answer at the fine ghost centres
+    fmask, cmask = written_masks(items, 1, cl, fl)
+    assert np.abs(f_gpu[fmask] - f[fmask]).max() <= 1e-13 * np.abs(f).max()
+    c_gpu = gpu_restrict(plan, f, c)
+    assert np.abs(c_gpu[cmask] - c[cmask]).max() <= 1e-13 * np.abs(c).max()
+
+
+def test_empty_plan():
+    plan = B.Plan([], 4, 16, 16, B.PREC_FP64)
+    c = torch.zeros(16, dtype=torch.float64, device="cuda")
+    f = torch.ones(16, dtype=torch.float64, device="cuda")
+    plan.interpolate(c, f)
+    plan.restrict(f, c)
+    torch.cuda.synchronize()
+    assert torch.all(f == 1) and torch.all(c == 0)
+    assert plan.info["interp_outputs"] == 0
+
+
+def test_overlapping_buffers_rejected():
+    items, cl, fl = wl.make_items([0], [-1], [6], [2], [2], 1)
+    plan = B.Plan(items, 1, cl, fl)
+    buf = torch.zeros(cl + fl, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.AmrError):
+        plan.interpolate(buf[:cl], buf[cl // 2:])
+
+
+def test_full_size_uniform_batch_sampled():
+    """2,048 hanging faces, p = 9, k = 3, U = 59, Taylor-3 (the benchmark
+    workload, same launch): 3,000 sampled outputs of each operator against
+    the oracle, one by one."""
+    items, coarse, fine = wl.uniform_batch(device="cuda")
+    U = 59
+    for precision, tol in ((B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND)):
+        plan = B.Plan(items, U, coarse.numel(), fine.numel(), precision)
+        f_out = fine.clone()
+        plan.interpolate(coarse, f_out)
+        c_out = coarse.clone()
+        plan.restrict(fine, c_out)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(11)
+        c_host, f_host = coarse.cpu().numpy(), fine.cpu().numpy()
+        f_gpu, c_gpu = f_out.cpu().numpy(), c_out.cpu().numpy()
+        p, k = 9, 3
+        arr = 2 * k * p * p * U
+        worst = 0.0
+        for _ in range(3000):
+            i = int(rng.integers(len(items)))
+            it = items[i]
+            s = int(rng.integers(9))
+            # a ghost volume of subface s: signed layer -1..-k, any tangential
+            face = int(it["face"])
+            n = face % 3
+            ext = [p, p, p]
+            ext[n] = 2 * k
+            j = int(rng.integers(1, k + 1))
+            idx = [int(rng.integers(p)) for _ in range(3)]
+            idx[n] = k - j if face < 3 else k - 1 + j
+            vol = (idx[2] * ext[1] + idx[1]) * ext[0] + idx[0]
+            u = int(rng.integers(U))
+            e = int(it["fine_offset"]) + s * arr + vol * U + u
+            ref = tr.interpolate_one(it, U, c_host, e)
+            scale = np.abs(c_host[int(it["coarse_offset"]):int(it["coarse_offset"]) + arr]).max()
+            worst = max(worst, abs(f_gpu[e] - ref) / scale)
+            # a coarse halo volume
+            idx = [int(rng.integers(p)) for _ in range(3)]
+            idx[n] = k + j - 1 if face < 3 else k - j
+            vol = (idx[2] * ext[1] + idx[1]) * ext[0] + idx[0]
+            ec = int(it["coarse_offset"]) + vol * U + u
+            ref = tr.restrict_one(it, U, f_host, ec)
+            worst = max(worst, abs(c_gpu[ec] - ref) / scale)
+        record(test="full_size_sampled", precision=precision, worst=worst)
+        assert worst <= tol, (precision, worst)
+        plan.close()
