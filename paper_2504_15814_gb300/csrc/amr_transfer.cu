@@ -27,7 +27,7 @@ amr_status cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 constexpr int kThreads = 256;
-constexpr int kSmemBudget = 48 * 1024;  // dynamic shared memory per interpolation CTA
+constexpr int kSmemBudget = 64 * 1024;  // dynamic shared memory per interpolation CTA
 
 std::mutex g_tables_mutex;
 std::vector<int> g_tables_ready;  // per device
@@ -143,9 +143,9 @@ amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_
   p->n_rtiles = (int)br.restrict_tiles.size();
   p->interp_smem = br.max_interp_smem;
   if (p->interp_smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(amr::interp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
+    cudaError_t e = cudaFuncSetAttribute(amr::interp_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(amr::interp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
+      e = cudaFuncSetAttribute(amr::interp_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
     if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaFuncSetAttribute"); }
   }
   p->info.num_items = desc->num_items;
@@ -176,9 +176,9 @@ amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coa
   if (p->n_itiles == 0) return AMR_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (p->precision == AMR_PREC_SPLIT)
-    amr::interp_kernel<true><<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
+    amr::interp_split_kernel<<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
   else
-    amr::interp_kernel<false><<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
+    amr::interp_f64_kernel<<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
   AMR_CUDA(cudaGetLastError());
   return AMR_OK;
 }

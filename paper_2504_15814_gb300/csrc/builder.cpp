@@ -234,36 +234,43 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
   }
 
   // Tiles and byte counts.
-  const int TMAX = 8;
-  std::map<std::tuple<int, int, int, int>, std::pair<int64_t, int64_t>> ref_cache;  // (p,k,order,sub) -> (interp refs, restrict refs)
+  const int TMAX = 12;
+  auto add_interp_tiles = [&](int64_t it, int sub, int slot, int alo, int ahi, int blo, int bhi, int p, int k, int m) {
+    for (int a0 = alo; a0 < ahi; a0 += TMAX)
+      for (int b0 = blo; b0 < bhi; b0 += TMAX) {
+        const int na = std::min(TMAX, ahi - a0), nb = std::min(TMAX, bhi - b0);
+        IRange rn, ra, rb;
+        interp_region(p, k, m, a0, na, b0, nb, rn, ra, rb);
+        const int64_t vols = (int64_t)(rn.hi - rn.lo + 1) * (ra.hi - ra.lo + 1) * (rb.hi - rb.lo + 1);
+        const int nu_max = (int)std::min<int64_t>(U, std::max<int64_t>(1, smem_budget / (vols * 8)));
+        const int nchunks = (int)((U + nu_max - 1) / nu_max);
+        const int nu = (int)((U + nchunks - 1) / nchunks);
+        for (int c = 0; c < nchunks; ++c) {
+          Tile t{};
+          t.item = (int32_t)it; t.sub = (int8_t)sub; t.slot = (int8_t)slot;
+          t.na = (int8_t)na; t.nb = (int8_t)nb; t.a0 = (int16_t)a0; t.b0 = (int16_t)b0;
+          t.u0 = (int16_t)(c * nu); t.nu = (int16_t)std::min<int64_t>(nu, U - c * nu);
+          r.interp_tiles.push_back(t);
+          r.max_interp_smem = std::max<int>(r.max_interp_smem, (int)(vols * t.nu * 8));
+        }
+      }
+  };
+  std::map<std::tuple<int, int, int, int>, int64_t> ref_cache;  // (p,k,order,sub) -> restriction references
   for (int64_t it = 0; it < desc.num_items; ++it) {
     const amr_transfer_item& x = desc.items[it];
     const int p = x.patch_size, k = x.overlap, m = x.order, w = p / 3;
     std::vector<char> cmark((size_t)2 * k * p * p, 0);
+    if (x.subface < 0) add_interp_tiles(it, -1, -1, 0, p, 0, p, p, k, m);
     for (int sl = 0; sl < (x.subface < 0 ? 9 : 1); ++sl) {
       const int sub = x.subface < 0 ? sl : x.subface;
       const int s0 = sub % 3, s1 = sub / 3;
+      if (x.subface >= 0) add_interp_tiles(it, sub, 0, s0 * w, (s0 + 1) * w, s1 * w, (s1 + 1) * w, p, k, m);
       for (int a0 = s0 * w; a0 < (s0 + 1) * w; a0 += TMAX)
         for (int b0 = s1 * w; b0 < (s1 + 1) * w; b0 += TMAX) {
-          const int na = std::min(TMAX, (s0 + 1) * w - a0), nb = std::min(TMAX, (s1 + 1) * w - b0);
-          // interpolation region -> unknown chunk from the shared-memory budget
-          IRange rn, ra, rb;
-          interp_region(p, k, m, a0, na, b0, nb, rn, ra, rb);
-          const int64_t vols = (int64_t)(rn.hi - rn.lo + 1) * (ra.hi - ra.lo + 1) * (rb.hi - rb.lo + 1);
-          int nu_max = (int)std::min<int64_t>(U, std::max<int64_t>(1, smem_budget / (vols * 8)));
-          const int nchunks = (int)((U + nu_max - 1) / nu_max);
-          const int nu = (int)((U + nchunks - 1) / nchunks);
-          for (int c = 0; c < nchunks; ++c) {
-            Tile t{};
-            t.item = (int32_t)it; t.sub = (int8_t)sub; t.slot = (int8_t)(x.subface < 0 ? sub : 0);
-            t.na = (int8_t)na; t.nb = (int8_t)nb; t.a0 = (int16_t)a0; t.b0 = (int16_t)b0;
-            t.u0 = (int16_t)(c * nu); t.nu = (int16_t)std::min<int64_t>(nu, U - c * nu);
-            r.interp_tiles.push_back(t);
-            r.max_interp_smem = std::max<int>(r.max_interp_smem, (int)(vols * t.nu * 8));
-          }
           Tile t{};
           t.item = (int32_t)it; t.sub = (int8_t)sub; t.slot = (int8_t)(x.subface < 0 ? sub : 0);
-          t.na = (int8_t)na; t.nb = (int8_t)nb; t.a0 = (int16_t)a0; t.b0 = (int16_t)b0;
+          t.na = (int8_t)std::min(TMAX, (s0 + 1) * w - a0); t.nb = (int8_t)std::min(TMAX, (s1 + 1) * w - b0);
+          t.a0 = (int16_t)a0; t.b0 = (int16_t)b0;
           for (int64_t u0 = 0; u0 < U; u0 += 128) {
             t.u0 = (int16_t)u0; t.nu = (int16_t)std::min<int64_t>(128, U - u0);
             r.restrict_tiles.push_back(t);
@@ -271,17 +278,15 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
         }
       for (int b = s1 * w; b < (s1 + 1) * w; ++b)
         for (int a = s0 * w; a < (s0 + 1) * w; ++a) mark_interp(cmark, p, k, m, a, b);
-      // restriction references (per subface fine array)
       auto key = std::make_tuple(p, k, m, sub);
       auto f = ref_cache.find(key);
       if (f == ref_cache.end()) {
         std::vector<char> fmark((size_t)2 * k * p * p, 0);
         for (int b = s1 * w; b < (s1 + 1) * w; ++b)
           for (int a = s0 * w; a < (s0 + 1) * w; ++a) mark_restrict(fmark, p, k, m, 3 * a + 1 - s0 * p, 3 * b + 1 - s1 * p);
-        int64_t cnt = std::count(fmark.begin(), fmark.end(), 1);
-        f = ref_cache.emplace(key, std::make_pair((int64_t)0, cnt)).first;
+        f = ref_cache.emplace(key, (int64_t)std::count(fmark.begin(), fmark.end(), 1)).first;
       }
-      r.restrict_bytes += f->second.second * U * 8;
+      r.restrict_bytes += f->second * U * 8;
       r.interp_outputs += (int64_t)k * p * p;
       r.restrict_outputs += (int64_t)k * w * w;
     }

@@ -14,6 +14,7 @@
 // base value; restriction stays float64 (see restrict_kernel).
 #pragma once
 #include "amr_common.cuh"
+#include "split_arith.cuh"
 
 namespace amr {
 
@@ -41,15 +42,16 @@ template <typename T>
 struct Tri { T m, z, p; };
 
 // ---------------------------------------------------------------------------
-// Taylor-m interpolation of one coarse centre and one unknown.
-// S(j, a, b): staged value (double).  Children: fine signed layer i in
-// [-k, -1] at normal offset e_n = i + 2 (units of h), tangential offsets
-// e0, e1 in {-1, 0, 1}.
+// Taylor-m interpolation of one coarse centre (layer -1, a, b) and one
+// unknown.  D(j, a', b') returns the input value (float64 path) or its
+// difference to the centre value (split path); c000 is the centre value or 0.
+// emit(ii, e0, e1, v) receives the Taylor value (or increment) of the child in
+// fine signed layer -1-ii (normal offset +1, 0, -1 for ii = 0, 1, 2, units of
+// h) and tangential offsets e0, e1 in {-1, 0, 1}.
 // ---------------------------------------------------------------------------
-template <int M, bool SPLIT, typename Stage, typename Out>
-__device__ __forceinline__ void taylor_interp_task(const Stage& S, const Out& out, int k, int p, int a, int b) {
-  using T = typename Arith<SPLIT>::T;
-  const T* wt = Arith<SPLIT>::wt_interp();
+template <int M, typename T, typename Diff, typename Emit>
+__device__ __forceinline__ void taylor_interp_core(const Diff& D, const Emit& emit, const T* __restrict__ wt,
+                                                   int k, int p, int a, int b, T c000) {
   const int c[3] = {-1, a, b};
   const int lo[3] = {-k, 0, 0};
   const int hi[3] = {k - 1, p - 1, p - 1};
@@ -59,13 +61,6 @@ __device__ __forceinline__ void taylor_interp_task(const Stage& S, const Out& ou
     stencil_window(c[d], lo[d], hi[d], pure_exactness(M), ps[d], pl[d]);
     stencil_window(c[d], lo[d], hi[d], mixed_exactness(M), ms[d], ml[d]);
   }
-  const double base = S(-1, a, b);
-  // D(x): input value, or its difference to the base in SPLIT mode.
-  auto D = [&](int j, int aa, int bb) -> T {
-    const double v = S(j, aa, bb);
-    if (SPLIT) return (T)(v - base);
-    return (T)v;
-  };
   auto W = [&](int L, int pos, int r) -> const T* { return wt + wt_offset(L) + (pos * 3 + r - 1) * L; };
 
   T C[M + 1][M + 1][M + 1];
@@ -75,66 +70,86 @@ __device__ __forceinline__ void taylor_interp_task(const Stage& S, const Out& ou
     for (int y = 0; y <= M; ++y)
 #pragma unroll
       for (int z = 0; z <= M; ++z) C[x][y][z] = T(0);
-  C[0][0][0] = SPLIT ? T(0) : (T)base;
+  C[0][0][0] = c000;
 
-  // pure derivatives along each axis
+  // pure derivatives along each axis: one pass over the window, all orders
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
+    const T* w1 = W(pl[d], c[d] - ps[d], 1);
+    T acc[M + 1];
+#pragma unroll
+    for (int r = 1; r <= M; ++r) acc[r] = T(0);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      if (i < pl[d]) {
+        int x[3] = {c[0], c[1], c[2]};
+        x[d] = ps[d] + i;
+        const T v = D(x[0], x[1], x[2]);
+#pragma unroll
+        for (int r = 1; r <= M; ++r) acc[r] += w1[(r - 1) * pl[d] + i] * v;
+      }
+    }
 #pragma unroll
     for (int r = 1; r <= M; ++r) {
-      const T* w = W(pl[d], c[d] - ps[d], r);
-      T acc = T(0);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        if (i < pl[d]) {
-          int x[3] = {c[0], c[1], c[2]};
-          x[d] = ps[d] + i;
-          acc += w[i] * D(x[0], x[1], x[2]);
-        }
-      }
-      if (d == 0) C[r][0][0] = acc;
-      if (d == 1) C[0][r][0] = acc;
-      if (d == 2) C[0][0][r] = acc;
+      if (d == 0) C[r][0][0] = acc[r];
+      if (d == 1) C[0][r][0] = acc[r];
+      if (d == 2) C[0][0][r] = acc[r];
     }
   }
-  // mixed derivatives over planes (d, e), orders (rd, re) with rd + re <= M
+  // mixed derivatives over the planes (d, e): 3x3 windows
 #pragma unroll
   for (int d = 0; d < 3; ++d)
 #pragma unroll
-    for (int e = d + 1; e < 3; ++e)
+    for (int e = d + 1; e < 3; ++e) {
+      const T* wd = W(ml[d], c[d] - ms[d], 1);  // rows r = 1, 2 follow at +3, +6
+      const T* we = W(ml[e], c[e] - ms[e], 1);
+      T acc11 = T(0), acc21 = T(0), acc12 = T(0);
 #pragma unroll
-      for (int rd = 1; rd < M; ++rd)
+      for (int q = 0; q < 3; ++q) {
+        // first collapse along d for this e-line
+        T s1 = T(0), s2 = T(0);
 #pragma unroll
-        for (int re = 1; re + rd <= M; ++re) {
-          const T* wd = W(ml[d], c[d] - ms[d], rd);
-          const T* we = W(ml[e], c[e] - ms[e], re);
-          T acc = T(0);
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              int x[3] = {c[0], c[1], c[2]};
-              x[d] = ms[d] + i;
-              x[e] = ms[e] + q;
-              acc += wd[i] * we[q] * D(x[0], x[1], x[2]);
-            }
-          int r3[3] = {0, 0, 0};
-          r3[d] = rd;
-          r3[e] = re;
-          C[r3[0]][r3[1]][r3[2]] = acc;
+        for (int i = 0; i < 3; ++i) {
+          int x[3] = {c[0], c[1], c[2]};
+          x[d] = ms[d] + i;
+          x[e] = ms[e] + q;
+          const T v = D(x[0], x[1], x[2]);
+          s1 += wd[i] * v;
+          if (M == 3) s2 += wd[3 + i] * v;
         }
-  if (M == 3) {  // u_{n t0 t1}
+        acc11 += we[q] * s1;
+        if (M == 3) {
+          acc21 += we[q] * s2;
+          acc12 += we[3 + q] * s1;
+        }
+      }
+      int r3[3] = {0, 0, 0};
+      r3[d] = 1; r3[e] = 1;
+      C[r3[0]][r3[1]][r3[2]] = acc11;
+      if (M == 3) {
+        r3[d] = 2; r3[e] = 1;
+        C[r3[0]][r3[1]][r3[2]] = acc21;
+        r3[d] = 1; r3[e] = 2;
+        C[r3[0]][r3[1]][r3[2]] = acc12;
+      }
+    }
+  if (M == 3) {  // u_{n t0 t1} on the 3x3x3 box
     const T* w0 = W(ml[0], c[0] - ms[0], 1);
     const T* w1 = W(ml[1], c[1] - ms[1], 1);
     const T* w2 = W(ml[2], c[2] - ms[2], 1);
     T acc = T(0);
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int q = 0; q < 3; ++q) {
+      T sq = T(0);
 #pragma unroll
-      for (int j = 0; j < 3; ++j)
+      for (int j = 0; j < 3; ++j) {
+        T sj = T(0);
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
-          acc += w0[i] * w1[j] * w2[q] * D(ms[0] + i, ms[1] + j, ms[2] + q);
+        for (int i = 0; i < 3; ++i) sj += w0[i] * D(ms[0] + i, ms[1] + j, ms[2] + q);
+        sq += w1[j] * sj;
+      }
+      acc += w2[q] * sq;
+    }
     C[1][1][1] = acc;
   }
 
@@ -155,16 +170,13 @@ __device__ __forceinline__ void taylor_interp_task(const Stage& S, const Out& ou
       R[y][z].p = (c0 + ev) + od;
       R[y][z].m = (c0 + ev) - od;
     }
-  // Children normal offsets: i = -1 -> +1, i = -2 -> 0, i = -3 -> -1.
 #pragma unroll
   for (int ii = 0; ii < 3; ++ii) {
     if (ii >= k) break;
-    const int i = -1 - ii;
-    // Step B (t0) for this e_n
-    Tri<T> Sg[M + 1];
+    auto pick = [&](const Tri<T>& t) -> T { return ii == 0 ? t.p : (ii == 1 ? t.z : t.m); };
+    Tri<T> Sg[M + 1];  // Step B (t0) for this normal offset
 #pragma unroll
     for (int z = 0; z <= M; ++z) {
-      auto pick = [&](const Tri<T>& t) -> T { return ii == 0 ? t.p : (ii == 1 ? t.z : t.m); };
       T ev = T(0), od = T(0);
 #pragma unroll
       for (int y = 2; y + z <= M; y += 2) ev += pick(R[y][z]);
@@ -176,7 +188,7 @@ __device__ __forceinline__ void taylor_interp_task(const Stage& S, const Out& ou
       Sg[z].m = (c0 + ev) - od;
     }
 #pragma unroll
-    for (int e0 = -1; e0 <= 1; ++e0) {
+    for (int e0 = -1; e0 <= 1; ++e0) {  // Step C (t1)
       T q[M + 1];
 #pragma unroll
       for (int z = 0; z <= M; ++z) q[z] = e0 < 0 ? Sg[z].m : (e0 == 0 ? Sg[z].z : Sg[z].p);
@@ -185,16 +197,9 @@ __device__ __forceinline__ void taylor_interp_task(const Stage& S, const Out& ou
       for (int z = 2; z <= M; z += 2) ev += q[z];
 #pragma unroll
       for (int z = 1; z <= M; z += 2) od += q[z];
-      const T vz = q[0], vp = (q[0] + ev) + od, vm = (q[0] + ev) - od;
-      if (SPLIT) {
-        out(i, a, b, e0, -1, base + (double)vm);
-        out(i, a, b, e0, 0, (ii == 1 && e0 == 0) ? base : base + (double)vz);
-        out(i, a, b, e0, 1, base + (double)vp);
-      } else {
-        out(i, a, b, e0, -1, (double)vm);
-        out(i, a, b, e0, 0, (double)vz);
-        out(i, a, b, e0, 1, (double)vp);
-      }
+      emit(ii, e0, -1, (q[0] + ev) - od);
+      emit(ii, e0, 0, q[0]);
+      emit(ii, e0, 1, (q[0] + ev) + od);
     }
   }
 }
@@ -212,23 +217,15 @@ __device__ __forceinline__ Tri<T> dlin3(T xm, T x0, T xp, bool lo_edge, bool hi_
   return r;
 }
 
-template <bool SPLIT, typename Stage, typename Out>
-__device__ __forceinline__ void dlinear_interp_task(const Stage& S, const Out& out, int k, int p, int a, int b) {
-  using T = typename Arith<SPLIT>::T;
-  const double base = S(-1, a, b);
-  auto D = [&](int j, int aa, int bb) -> T {
-    const double v = S(j, aa, bb);
-    if (SPLIT) return (T)(v - base);
-    return (T)v;
-  };
+// d-linear interpolation of one coarse centre: the normal lerp on the 3x3
+// neighbour columns, then along t0, then along t1 (the tensor product
+// P = P_t1 P_t0 P_n of Sec. 2, sum-factorised).  Same D / emit contract.
+template <typename T, typename Diff, typename Emit>
+__device__ __forceinline__ void dlinear_interp_core(const Diff& D, const Emit& emit, int k, int p, int a, int b) {
   const bool alo = a == 0, ahi = a == p - 1, blo = b == 0, bhi = b == p - 1;
-  const int am = alo ? a : a - 1, ap = ahi ? a : a + 1;
-  const int bm = blo ? b : b - 1, bp = bhi ? b : b + 1;
+  const int aidx[3] = {alo ? a : a - 1, a, ahi ? a : a + 1};
+  const int bidx[3] = {blo ? b : b - 1, b, bhi ? b : b + 1};
   const T third = T(1) / T(3);
-  const int aidx[3] = {am, a, ap};
-  const int bidx[3] = {bm, b, bp};
-  // normal pass per tangential neighbour column: child layer -1 (offset +1/3 H
-  // towards layer 0), -2 (coincident with layer -1), -3 (towards layer -2)
   T N[3][3][3];  // [child normal ii][da][db]
 #pragma unroll
   for (int da = 0; da < 3; ++da)
@@ -236,47 +233,58 @@ __device__ __forceinline__ void dlinear_interp_task(const Stage& S, const Out& o
     for (int db = 0; db < 3; ++db) {
       const T v1 = D(-1, aidx[da], bidx[db]);
       const T v0 = D(0, aidx[da], bidx[db]);
-      N[0][da][db] = v1 + third * (v0 - v1);
-      N[1][da][db] = v1;
-      if (k >= 3) {
-        const T v2 = D(-2, aidx[da], bidx[db]);
-        N[2][da][db] = v1 + third * (v2 - v1);
-      } else {
-        N[2][da][db] = v1;
-      }
+      N[0][da][db] = v1 + third * (v0 - v1);  // fine layer -1: towards coarse layer 0
+      N[1][da][db] = v1;                      // fine layer -2: coincident with coarse layer -1
+      N[2][da][db] = v1;
+      if (k >= 3) N[2][da][db] = v1 + third * (D(-2, aidx[da], bidx[db]) - v1);  // fine layer -3
     }
 #pragma unroll
   for (int ii = 0; ii < 3; ++ii) {
     if (ii >= k) break;
-    const int i = -1 - ii;
-    Tri<T> A[3];  // per db: children along t0
+    Tri<T> A[3];
 #pragma unroll
     for (int db = 0; db < 3; ++db) A[db] = dlin3<T>(N[ii][0][db], N[ii][1][db], N[ii][2][db], alo, ahi);
 #pragma unroll
     for (int e0 = -1; e0 <= 1; ++e0) {
       auto pick = [&](const Tri<T>& t) -> T { return e0 < 0 ? t.m : (e0 == 0 ? t.z : t.p); };
       const Tri<T> r = dlin3<T>(pick(A[0]), pick(A[1]), pick(A[2]), blo, bhi);
-      if (SPLIT) {
-        out(i, a, b, e0, -1, base + (double)r.m);
-        out(i, a, b, e0, 0, (ii == 1 && e0 == 0) ? base : base + (double)r.z);
-        out(i, a, b, e0, 1, base + (double)r.p);
-      } else {
-        out(i, a, b, e0, -1, (double)r.m);
-        out(i, a, b, e0, 0, (double)r.z);
-        out(i, a, b, e0, 1, (double)r.p);
-      }
+      emit(ii, e0, -1, r.m);
+      emit(ii, e0, 0, r.z);
+      emit(ii, e0, 1, r.p);
     }
   }
 }
 
+// Where the fine children of coarse centre (a, b) live: the fine face array
+// (slot) and the offset of tangential index 0 of that subface.
+struct ChildMap {
+  int slot, q0_off, q1_off;
+};
+__device__ __forceinline__ ChildMap child_map(const Tile& t, int p, int a, int b) {
+  ChildMap m;
+  int s0, s1;
+  if (t.sub >= 0) {
+    s0 = t.sub % 3;
+    s1 = t.sub / 3;
+    m.slot = t.slot;
+  } else {  // whole-face tile: the subface follows from the centre
+    const int w = p / 3;
+    s0 = a / w;
+    s1 = b / w;
+    m.slot = s0 + 3 * s1;
+  }
+  m.q0_off = 1 - s0 * p;
+  m.q1_off = 1 - s1 * p;
+  return m;
+}
+
 // ---------------------------------------------------------------------------
-// Interpolation kernel: one CTA per tile.
+// Float64 interpolation kernel: one CTA per tile, region staged as doubles.
 // ---------------------------------------------------------------------------
-template <bool SPLIT>
-__global__ void __launch_bounds__(256) interp_kernel(const amr_transfer_item* __restrict__ items,
-                                                     const Tile* __restrict__ tiles, int U,
-                                                     const double* __restrict__ coarse,
-                                                     double* __restrict__ fine) {
+__global__ void __launch_bounds__(256) interp_f64_kernel(const amr_transfer_item* __restrict__ items,
+                                                         const Tile* __restrict__ tiles, int U,
+                                                         const double* __restrict__ coarse,
+                                                         double* __restrict__ fine) {
   extern __shared__ double smem[];
   const Tile t = tiles[blockIdx.x];
   const amr_transfer_item it = items[t.item];
@@ -299,23 +307,82 @@ __global__ void __launch_bounds__(256) interp_kernel(const amr_transfer_item* __
   }
   __syncthreads();
   const int64_t arr = fr.vols * U;
-  double* fb = fine + it.fine_offset + (int64_t)t.slot * arr + t.u0;
-  const int s0 = t.sub % 3, s1 = t.sub / 3;
   const int ntask = t.na * t.nb * nu;
   for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
     const int u = e % nu;
     const int ci = e / nu;
     const int a = t.a0 + ci % t.na, b = t.b0 + ci / t.na;
-    auto S = [&](int j, int aa, int bb) -> double {
+    const ChildMap cm = child_map(t, p, a, b);
+    double* fb = fine + it.fine_offset + (int64_t)cm.slot * arr + t.u0 + u;
+    auto D = [&](int j, int aa, int bb) -> double {
       return smem[(((j - rn.lo) * NB + (bb - rb.lo)) * NA + (aa - ra.lo)) * nu + u];
     };
-    auto O = [&](int i, int a_, int b_, int e0, int e1, double val) {
-      const int q0 = 3 * a_ + 1 + e0 - s0 * p, q1 = 3 * b_ + 1 + e1 - s1 * p;
-      fb[frame_vol(fr, i, q0, q1) * U + u] = val;
+    auto emit = [&](int ii, int e0, int e1, double v) {
+      fb[frame_vol(fr, -1 - ii, 3 * a + e0 + cm.q0_off, 3 * b + e1 + cm.q1_off) * U] = v;
     };
-    if (m == 3) taylor_interp_task<3, SPLIT>(S, O, k, p, a, b);
-    else if (m == 2) taylor_interp_task<2, SPLIT>(S, O, k, p, a, b);
-    else dlinear_interp_task<SPLIT>(S, O, k, p, a, b);
+    if (m == 3) taylor_interp_core<3, double>(D, emit, c_wt_interp, k, p, a, b, D(-1, a, b));
+    else if (m == 2) taylor_interp_core<2, double>(D, emit, c_wt_interp, k, p, a, b, D(-1, a, b));
+    else dlinear_interp_core<double>(D, emit, k, p, a, b);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split-precision interpolation kernel: the region is staged as exact float
+// pairs (split with integer operations), the stencil differences are formed
+// from the pairs, the derivative and Taylor arithmetic runs in float32, and
+// each child is rebuilt as a float64 from the base pair and its increment.
+// The child coincident with the centre is the centre's float64 value itself.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) interp_split_kernel(const amr_transfer_item* __restrict__ items,
+                                                           const Tile* __restrict__ tiles, int U,
+                                                           const double* __restrict__ coarse,
+                                                           double* __restrict__ fine) {
+  extern __shared__ double smem_raw[];
+  F2* sm = reinterpret_cast<F2*>(smem_raw);
+  const Tile t = tiles[blockIdx.x];
+  const amr_transfer_item it = items[t.item];
+  const int p = it.patch_size, k = it.overlap, m = it.order;
+  const FaceFrame fr = face_frame(it.face, p, k);
+  IRange rn, ra, rb;
+  interp_region(p, k, m, t.a0, t.na, t.b0, t.nb, rn, ra, rb);
+  const int NA = ra.hi - ra.lo + 1, NB = rb.hi - rb.lo + 1, NJ = rn.hi - rn.lo + 1;
+  const int nu = t.nu;
+  const int total = NJ * NB * NA * nu;
+  const double* cb = coarse + it.coarse_offset + t.u0;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int u = e % nu;
+    int v = e / nu;
+    const int aa = v % NA;
+    v /= NA;
+    const int bb = v % NB;
+    const int jj = v / NB;
+    sm[e] = split_f64(__ldg(cb + frame_vol(fr, rn.lo + jj, ra.lo + aa, rb.lo + bb) * U + u));
+  }
+  __syncthreads();
+  const int64_t arr = fr.vols * U;
+  const int ntask = t.na * t.nb * nu;
+  for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
+    const int u = e % nu;
+    const int ci = e / nu;
+    const int a = t.a0 + ci % t.na, b = t.b0 + ci / t.na;
+    const ChildMap cm = child_map(t, p, a, b);
+    double* fb = fine + it.fine_offset + (int64_t)cm.slot * arr + t.u0 + u;
+    auto S = [&](int j, int aa, int bb) -> F2 {
+      return sm[(((j - rn.lo) * NB + (bb - rb.lo)) * NA + (aa - ra.lo)) * nu + u];
+    };
+    const F2 hc = S(-1, a, b);
+    const double base = __ldg(cb + frame_vol(fr, -1, a, b) * U + u);
+    auto D = [&](int j, int aa, int bb) -> float {
+      const F2 x = S(j, aa, bb);
+      return __fadd_rn(__fsub_rn(x.hi, hc.hi), __fsub_rn(x.lo, hc.lo));
+    };
+    auto emit = [&](int ii, int e0, int e1, float incr) {
+      const double v = (ii == 1 && e0 == 0 && e1 == 0) ? base : add_back(hc, incr);
+      fb[frame_vol(fr, -1 - ii, 3 * a + e0 + cm.q0_off, 3 * b + e1 + cm.q1_off) * U] = v;
+    };
+    if (m == 3) taylor_interp_core<3, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
+    else if (m == 2) taylor_interp_core<2, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
+    else dlinear_interp_core<float>(D, emit, k, p, a, b);
   }
 }
 

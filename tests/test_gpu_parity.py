@@ -183,3 +183,28 @@ def test_full_size_uniform_batch_sampled():
         record(test="full_size_sampled", precision=precision, worst=worst)
         assert worst <= tol, (precision, worst)
         plan.close()
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_split_adversarial_magnitudes(order):
+    """Split path on fields whose unknowns span 1e-20 .. 1e20, include exact
+    powers of two, constants, zeros and sign changes: the exact float-pair
+    split and the integer float64 assembly keep the normwise error bound."""
+    U = 12
+    n = 6
+    items, cl, fl = wl.make_items(list(range(6)), [-1] * n, [6] * n, [3] * n, [order] * n, U)
+    rng = np.random.Generator(np.random.PCG64(77 + order))
+    field = wl.SmoothField(U, rng)
+    coarse, fine = wl.sample_buffers(items, U, cl, fl, field, wl.origins_in_box(n, rng))
+    scales = torch.tensor([1e-20, 1e-8, 1.0, 3.0e5, 1e12, 1e20, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0], dtype=torch.float64)
+    c = coarse.view(-1, U) * scales
+    f = fine.view(-1, U) * scales
+    c[:, 6] = 0.0
+    f[:, 6] = 0.0
+    c[:, 7] = 2.0 ** 10
+    f[:, 7] = 2.0 ** 10
+    c[:, 8] = torch.where(c[:, 8] > 0, 2.0 ** -3, -(2.0 ** 7))
+    f[:, 8] = torch.where(f[:, 8] > 0, 2.0 ** -3, -(2.0 ** 7))
+    c[:, 9] = 1.0 + c[:, 9] * 1e-12
+    f[:, 9] = 1.0 + f[:, 9] * 1e-12
+    _check(items, U, c.reshape(-1).numpy(), f.reshape(-1).numpy(), B.PREC_SPLIT, SPLIT_BOUND)
