@@ -44,18 +44,18 @@ struct FaceFrame {
 };
 
 __host__ __device__ inline FaceFrame face_frame(int face, int p, int k) {
+  // extents: 2k along the normal axis n = face % 3, p along the others;
+  // strides of a lexicographic box with x fastest (selects, no local arrays)
   const int n = face % 3;
-  const int t0 = (n == 0) ? 1 : 0;
-  const int t1 = (n == 2) ? 1 : 2;
-  int64_t ext[3] = {p, p, p};
-  ext[n] = 2 * k;
-  const int64_t stride[3] = {1, ext[0], ext[0] * ext[1]};
+  const int64_t ex = n == 0 ? 2 * k : p, ey = n == 1 ? 2 * k : p, ez = n == 2 ? 2 * k : p;
+  const int64_t sy = ex, sz = ex * ey;
+  const int64_t sn = n == 0 ? 1 : (n == 1 ? sy : sz);
   FaceFrame f;
-  f.s_n = (face < 3) ? stride[n] : -stride[n];
-  f.base_n = (face < 3) ? (int64_t)k * stride[n] : (int64_t)(k - 1) * stride[n];
-  f.s_t0 = stride[t0];
-  f.s_t1 = stride[t1];
-  f.vols = ext[0] * ext[1] * ext[2];
+  f.s_n = (face < 3) ? sn : -sn;
+  f.base_n = (face < 3) ? (int64_t)k * sn : (int64_t)(k - 1) * sn;
+  f.s_t0 = n == 0 ? sy : 1;   // t0 = y for normal x, else x
+  f.s_t1 = n == 2 ? sy : sz;  // t1 = y for normal z, else z
+  f.vols = ex * ey * ez;
   return f;
 }
 
@@ -138,5 +138,12 @@ constexpr int WT_SIZE = 150;
 // layers 0..k-1, or layers -1, 0 when k = 1).
 constexpr int LS_SIZE = 3 * 3 * 3;
 __host__ __device__ inline int ls_index(int k, int j, int i) { return ((k - 1) * 3 + j) * 3 + i; }
+
+// Combined Taylor restriction weights: coarse halo layer j >= 1 of a face with
+// overlap k (2 or 3) and order m (2 or 3) is sum_i W[i] u(fine layer s + i)
+// over the derivative window (s, L) about fine layer k - 1 (Sec. 3: Taylor
+// about the nearest fine cell, extrapolated by (3j + 2 - k) h).
+constexpr int RW_SIZE = 8 * 5;
+__host__ __device__ inline int rw_index(int order, int k, int j) { return (((order - 2) * 2 + (k - 2)) * 2 + (j - 1)) * 5; }
 
 }  // namespace amr

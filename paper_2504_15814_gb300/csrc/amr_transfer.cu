@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -42,6 +43,10 @@ amr_status upload_tables(int device) {
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_wt_interp_f, t.wt_interp_f, sizeof t.wt_interp_f));
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_wt_restrict_f, t.wt_restrict_f, sizeof t.wt_restrict_f));
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_ls, t.ls, sizeof t.ls));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_ls_f, t.ls_f, sizeof t.ls_f));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw, t.rw, sizeof t.rw));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw_hi, t.rw_hi, sizeof t.rw_hi));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw_lo, t.rw_lo, sizeof t.rw_lo));
   g_tables_ready[device] = 1;
   return AMR_OK;
 }
@@ -75,7 +80,7 @@ struct amr_transfer_plan {
   amr::Tile* itiles_d = nullptr;
   amr::Tile* rtiles_d = nullptr;
   int n_itiles = 0, n_rtiles = 0;
-  int interp_smem = 0;
+  int interp_smem = 0;  // bytes of dynamic shared memory per interpolation CTA
   amr_transfer_plan_info info{};
 };
 
@@ -143,9 +148,9 @@ amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_
   p->n_rtiles = (int)br.restrict_tiles.size();
   p->interp_smem = br.max_interp_smem;
   if (p->interp_smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(amr::interp_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
+    cudaError_t e = cudaFuncSetAttribute(amr::interp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(amr::interp_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
+      e = cudaFuncSetAttribute(amr::interp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
     if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaFuncSetAttribute"); }
   }
   p->info.num_items = desc->num_items;
@@ -176,9 +181,9 @@ amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coa
   if (p->n_itiles == 0) return AMR_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (p->precision == AMR_PREC_SPLIT)
-    amr::interp_split_kernel<<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
+    amr::interp_kernel<true><<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
   else
-    amr::interp_f64_kernel<<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
+    amr::interp_kernel<false><<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
   AMR_CUDA(cudaGetLastError());
   return AMR_OK;
 }

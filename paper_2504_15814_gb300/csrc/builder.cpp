@@ -89,10 +89,34 @@ Tables make_tables() {
       }
     }
   }
+  // Combined restriction weights (exact): W[i] = [s + i == k - 1] +
+  // sum_r coeff_r(i) e^r with coeff_r the Taylor coefficient weights about
+  // fine layer k - 1 on the window (s, L) and e = 3j + 2 - k.
+  for (int order = 2; order <= 3; ++order)
+    for (int k = 2; k <= 3; ++k)
+      for (int j = 1; j < k; ++j) {
+        int s0, L;
+        stencil_window(k - 1, -k, k - 1, pure_exactness(order), s0, L);
+        const int pos = k - 1 - s0;
+        const int e = 3 * j + 2 - k;
+        for (int i = 0; i < 5; ++i) {
+          Q w(0);
+          if (i < L) {
+            if (i == pos) w = w + Q(1);
+            Q epow(1);
+            for (int r = 1; r <= order; ++r) {
+              epow = epow * Q(e);
+              w = w + lagrange_taylor_coeff(L, pos, r, i) * epow;
+            }
+          }
+          const int idx = rw_index(order, k, j) + i;
+          t.rw[idx] = w.to_double();
+          t.rw_hi[idx] = (float)t.rw[idx];
+          t.rw_lo[idx] = (float)(t.rw[idx] - (double)t.rw_hi[idx]);
+        }
+      }
   return t;
 }
-
-bool overlaps(int64_t a0, int64_t a1, int64_t b0, int64_t b1) { return a0 < b1 && b0 < a1; }
 
 // Mark the volumes one interpolation centre references; reference volume index
 // (j + k) * p * p + b * p + a.
@@ -255,27 +279,33 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
         }
       }
   };
+  auto add_restrict_tiles = [&](int64_t it, int sub, int slot, int alo, int ahi, int blo, int bhi) {
+    for (int a0 = alo; a0 < ahi; a0 += TMAX)
+      for (int b0 = blo; b0 < bhi; b0 += TMAX) {
+        Tile t{};
+        t.item = (int32_t)it; t.sub = (int8_t)sub; t.slot = (int8_t)slot;
+        t.na = (int8_t)std::min(TMAX, ahi - a0); t.nb = (int8_t)std::min(TMAX, bhi - b0);
+        t.a0 = (int16_t)a0; t.b0 = (int16_t)b0;
+        for (int64_t u0 = 0; u0 < U; u0 += 128) {
+          t.u0 = (int16_t)u0; t.nu = (int16_t)std::min<int64_t>(128, U - u0);
+          r.restrict_tiles.push_back(t);
+        }
+      }
+  };
   std::map<std::tuple<int, int, int, int>, int64_t> ref_cache;  // (p,k,order,sub) -> restriction references
   for (int64_t it = 0; it < desc.num_items; ++it) {
     const amr_transfer_item& x = desc.items[it];
     const int p = x.patch_size, k = x.overlap, m = x.order, w = p / 3;
     std::vector<char> cmark((size_t)2 * k * p * p, 0);
-    if (x.subface < 0) add_interp_tiles(it, -1, -1, 0, p, 0, p, p, k, m);
+    if (x.subface < 0) {
+      add_interp_tiles(it, -1, -1, 0, p, 0, p, p, k, m);
+      add_restrict_tiles(it, -1, -1, 0, p, 0, p);
+    }
     for (int sl = 0; sl < (x.subface < 0 ? 9 : 1); ++sl) {
       const int sub = x.subface < 0 ? sl : x.subface;
       const int s0 = sub % 3, s1 = sub / 3;
       if (x.subface >= 0) add_interp_tiles(it, sub, 0, s0 * w, (s0 + 1) * w, s1 * w, (s1 + 1) * w, p, k, m);
-      for (int a0 = s0 * w; a0 < (s0 + 1) * w; a0 += TMAX)
-        for (int b0 = s1 * w; b0 < (s1 + 1) * w; b0 += TMAX) {
-          Tile t{};
-          t.item = (int32_t)it; t.sub = (int8_t)sub; t.slot = (int8_t)(x.subface < 0 ? sub : 0);
-          t.na = (int8_t)std::min(TMAX, (s0 + 1) * w - a0); t.nb = (int8_t)std::min(TMAX, (s1 + 1) * w - b0);
-          t.a0 = (int16_t)a0; t.b0 = (int16_t)b0;
-          for (int64_t u0 = 0; u0 < U; u0 += 128) {
-            t.u0 = (int16_t)u0; t.nu = (int16_t)std::min<int64_t>(128, U - u0);
-            r.restrict_tiles.push_back(t);
-          }
-        }
+      if (x.subface >= 0) add_restrict_tiles(it, sub, 0, s0 * w, (s0 + 1) * w, s1 * w, (s1 + 1) * w);
       for (int b = s1 * w; b < (s1 + 1) * w; ++b)
         for (int a = s0 * w; a < (s0 + 1) * w; ++a) mark_interp(cmark, p, k, m, a, b);
       auto key = std::make_tuple(p, k, m, sub);

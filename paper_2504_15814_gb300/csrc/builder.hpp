@@ -23,6 +23,9 @@ struct Tables {
   float wt_restrict_f[WT_SIZE];
   double ls[LS_SIZE];
   float ls_f[LS_SIZE];
+  double rw[RW_SIZE];     // combined restriction weights
+  float rw_hi[RW_SIZE];   // float pair of the same: rw = rw_hi + rw_lo (+ O(2^-48))
+  float rw_lo[RW_SIZE];
 };
 
 // Built once per process.

@@ -82,14 +82,39 @@ __device__ __forceinline__ double pair_to_f64(float s, float e) {
   return __longlong_as_double(bits);
 }
 
+// s + e = a + b exactly when |a| >= |b| (Dekker FastTwoSum).
+__device__ __forceinline__ float fast_two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+  return s;
+}
+
 // base + incr as float64, base given by its split pair (error < 2^-46 |base|
-// from the split, plus float32 rounding of the small correction terms).
+// from the split, plus float32 rounding of the small correction terms).  The
+// second renormalisation uses FastTwoSum: its precondition |s1| >= |t| fails
+// only when the result is 2^23 times smaller than the base, and then the
+// error stays below 2^-47 |base|.
 __device__ __forceinline__ double add_back(F2 base, float incr) {
   float e1, e2;
   const float s1 = two_sum(base.hi, incr, e1);
   const float t = __fadd_rn(e1, base.lo);
-  const float s2 = two_sum(s1, t, e2);
+  const float s2 = fast_two_sum(s1, t, e2);
   return pair_to_f64(s2, e2);
+}
+
+// Exact float64 value of a float, assembled from its bits with integer
+// operations (float-to-double conversion runs on the float64 unit on GB300).
+// Float denormals become signed zero.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t mag = b & 0x7fffffffu;
+  uint32_t hi = (b & 0x80000000u) | ((mag >> 3) + (896u << 20));
+  uint32_t lo = b << 29;
+  if (mag < 0x00800000u) {
+    hi = b & 0x80000000u;
+    lo = 0u;
+  }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 }  // namespace amr

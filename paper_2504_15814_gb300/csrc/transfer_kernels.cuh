@@ -8,13 +8,17 @@
 // k * 3 * 3 fine children.  Restriction needs no staging: one thread per
 // (coarse halo column, unknown) reads the coincident fine normal line.
 //
-// Precision: FP64 computes everything in float64.  SPLIT forms the stencil
-// differences u_j - u_c in float64, does the interpolation's derivative and
-// Taylor arithmetic in float32 and adds the increment back to the float64
-// base value; restriction stays float64 (see restrict_kernel).
+// Precision: FP64 computes everything in float64.  SPLIT keeps float64
+// instructions out of the kernels: inputs are split exactly into float pairs,
+// differences to the base value are formed from the pairs, interpolation
+// increments are float32, Taylor restriction (large extrapolation weights)
+// uses float-pair arithmetic, and outputs are rebuilt as float64 by integer
+// assembly.
 #pragma once
 #include "amr_common.cuh"
 #include "split_arith.cuh"
+
+#include <type_traits>
 
 namespace amr {
 
@@ -23,6 +27,10 @@ __constant__ double c_wt_restrict[WT_SIZE];
 __constant__ float c_wt_interp_f[WT_SIZE];
 __constant__ float c_wt_restrict_f[WT_SIZE];
 __constant__ double c_ls[LS_SIZE];
+__constant__ float c_ls_f[LS_SIZE];
+__constant__ double c_rw[RW_SIZE];
+__constant__ float c_rw_hi[RW_SIZE];
+__constant__ float c_rw_lo[RW_SIZE];
 
 template <bool SPLIT> struct Arith;
 template <> struct Arith<false> {
@@ -278,67 +286,45 @@ __device__ __forceinline__ ChildMap child_map(const Tile& t, int p, int a, int b
   return m;
 }
 
-// ---------------------------------------------------------------------------
-// Float64 interpolation kernel: one CTA per tile, region staged as doubles.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) interp_f64_kernel(const amr_transfer_item* __restrict__ items,
-                                                         const Tile* __restrict__ tiles, int U,
-                                                         const double* __restrict__ coarse,
-                                                         double* __restrict__ fine) {
-  extern __shared__ double smem[];
-  const Tile t = tiles[blockIdx.x];
-  const amr_transfer_item it = items[t.item];
-  const int p = it.patch_size, k = it.overlap, m = it.order;
-  const FaceFrame fr = face_frame(it.face, p, k);
-  IRange rn, ra, rb;
-  interp_region(p, k, m, t.a0, t.na, t.b0, t.nb, rn, ra, rb);
-  const int NA = ra.hi - ra.lo + 1, NB = rb.hi - rb.lo + 1, NJ = rn.hi - rn.lo + 1;
-  const int nu = t.nu;
-  const int total = NJ * NB * NA * nu;
-  const double* cb = coarse + it.coarse_offset + t.u0;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int u = e % nu;
-    int v = e / nu;
-    const int aa = v % NA;
-    v /= NA;
-    const int bb = v % NB;
-    const int jj = v / NB;
-    smem[e] = __ldg(cb + frame_vol(fr, rn.lo + jj, ra.lo + aa, rb.lo + bb) * U + u);
+// Mixed-radix counter over (u, x, y, z) with radices (nu, NX, NY, -): walks
+// e, e + step, ... without integer divisions in the loop.
+struct Counter4 {
+  int u, x, y, z;
+  int su, sx, sy, sz;
+  __device__ void init(int e, int step, int nu, int NX, int NY) {
+    u = e % nu; int v = e / nu; x = v % NX; v /= NX; y = v % NY; z = v / NY;
+    su = step % nu; int w = step / nu; sx = w % NX; w /= NX; sy = w % NY; sz = w / NY;
   }
-  __syncthreads();
-  const int64_t arr = fr.vols * U;
-  const int ntask = t.na * t.nb * nu;
-  for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
-    const int u = e % nu;
-    const int ci = e / nu;
-    const int a = t.a0 + ci % t.na, b = t.b0 + ci / t.na;
-    const ChildMap cm = child_map(t, p, a, b);
-    double* fb = fine + it.fine_offset + (int64_t)cm.slot * arr + t.u0 + u;
-    auto D = [&](int j, int aa, int bb) -> double {
-      return smem[(((j - rn.lo) * NB + (bb - rb.lo)) * NA + (aa - ra.lo)) * nu + u];
-    };
-    auto emit = [&](int ii, int e0, int e1, double v) {
-      fb[frame_vol(fr, -1 - ii, 3 * a + e0 + cm.q0_off, 3 * b + e1 + cm.q1_off) * U] = v;
-    };
-    if (m == 3) taylor_interp_core<3, double>(D, emit, c_wt_interp, k, p, a, b, D(-1, a, b));
-    else if (m == 2) taylor_interp_core<2, double>(D, emit, c_wt_interp, k, p, a, b, D(-1, a, b));
-    else dlinear_interp_core<double>(D, emit, k, p, a, b);
+  __device__ __forceinline__ void advance(int nu, int NX, int NY) {
+    u += su; int c = u >= nu; u -= c ? nu : 0;
+    x += sx + c; c = x >= NX; x -= c ? NX : 0;
+    y += sy + c; c = y >= NY; y -= c ? NY : 0;
+    z += sz + c;
   }
-}
+};
 
 // ---------------------------------------------------------------------------
-// Split-precision interpolation kernel: the region is staged as exact float
-// pairs (split with integer operations), the stencil differences are formed
-// from the pairs, the derivative and Taylor arithmetic runs in float32, and
-// each child is rebuilt as a float64 from the base pair and its increment.
-// The child coincident with the centre is the centre's float64 value itself.
+// Interpolation kernel: one CTA per tile (a rectangle of coarse centres of one
+// face and a chunk of unknowns).  Phase 1 stages the stencil region in shared
+// memory (float64, or exact float pairs in split mode); phase 2 runs one thread
+// per (centre, unknown).
+// Split mode: the stencil differences come from the pairs and the derivative
+// and Taylor arithmetic is float32; the child coincident with the centre is
+// the centre's own float64 value; the other children are rebuilt as float64
+// from base + increment, two thirds of them (tangential offset e1 <= 0) by one
+// float64 add of the exactly converted increment, the rest by TwoSum +
+// integer assembly without any float64 instruction -- this balances the
+// GB300 float64 unit (about 1/73 of the float32 rate) against the
+// integer/float32 issue slots.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) interp_split_kernel(const amr_transfer_item* __restrict__ items,
-                                                           const Tile* __restrict__ tiles, int U,
-                                                           const double* __restrict__ coarse,
-                                                           double* __restrict__ fine) {
+template <bool SPLIT>
+__global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_transfer_item* __restrict__ items,
+                                                     const Tile* __restrict__ tiles, int U,
+                                                     const double* __restrict__ coarse,
+                                                     double* __restrict__ fine) {
+  using SType = typename std::conditional<SPLIT, F2, double>::type;
   extern __shared__ double smem_raw[];
-  F2* sm = reinterpret_cast<F2*>(smem_raw);
+  SType* sm = reinterpret_cast<SType*>(smem_raw);
   const Tile t = tiles[blockIdx.x];
   const amr_transfer_item it = items[t.item];
   const int p = it.patch_size, k = it.overlap, m = it.order;
@@ -347,105 +333,175 @@ __global__ void __launch_bounds__(256) interp_split_kernel(const amr_transfer_it
   interp_region(p, k, m, t.a0, t.na, t.b0, t.nb, rn, ra, rb);
   const int NA = ra.hi - ra.lo + 1, NB = rb.hi - rb.lo + 1, NJ = rn.hi - rn.lo + 1;
   const int nu = t.nu;
-  const int total = NJ * NB * NA * nu;
+  // 32-bit element strides inside one face array (< 2^31 elements, checked on the host)
+  const int gs_n = (int)fr.s_n * U, gs_a = (int)fr.s_t0 * U, gs_b = (int)fr.s_t1 * U;
   const double* cb = coarse + it.coarse_offset + t.u0;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int u = e % nu;
-    int v = e / nu;
-    const int aa = v % NA;
-    v /= NA;
-    const int bb = v % NB;
-    const int jj = v / NB;
-    sm[e] = split_f64(__ldg(cb + frame_vol(fr, rn.lo + jj, ra.lo + aa, rb.lo + bb) * U + u));
+  {
+    const double* g0 = cb + frame_vol(fr, rn.lo, ra.lo, rb.lo) * U;
+    const int total = NJ * NB * NA * nu;
+    Counter4 c;
+    c.init(threadIdx.x, blockDim.x, nu, NA, NB);
+    // batches of STAGE loads in flight per thread before any conversion
+    constexpr int STAGE = 8;
+    for (int e0 = threadIdx.x; e0 < total; e0 += STAGE * blockDim.x) {
+      double v[STAGE];
+#pragma unroll
+      for (int q = 0; q < STAGE; ++q) {
+        if (e0 + q * (int)blockDim.x < total) v[q] = __ldg(g0 + c.z * gs_n + c.y * gs_b + c.x * gs_a + c.u);
+        c.advance(nu, NA, NB);
+      }
+#pragma unroll
+      for (int q = 0; q < STAGE; ++q) {
+        const int e = e0 + q * blockDim.x;
+        if (e < total) {
+          if constexpr (SPLIT) sm[e] = split_f64(v[q]);
+          else sm[e] = v[q];
+        }
+      }
+    }
   }
   __syncthreads();
   const int64_t arr = fr.vols * U;
+  const int SA = nu, SB = NA * nu, SJ = NB * NA * nu;
   const int ntask = t.na * t.nb * nu;
-  for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
-    const int u = e % nu;
-    const int ci = e / nu;
-    const int a = t.a0 + ci % t.na, b = t.b0 + ci / t.na;
+  Counter4 c;
+  c.init(threadIdx.x, blockDim.x, nu, t.na, t.nb);
+  for (int e = threadIdx.x; e < ntask; e += blockDim.x, c.advance(nu, t.na, t.nb)) {
+    const int u = c.u, a = t.a0 + c.x, b = t.b0 + c.y;
     const ChildMap cm = child_map(t, p, a, b);
-    double* fb = fine + it.fine_offset + (int64_t)cm.slot * arr + t.u0 + u;
-    auto S = [&](int j, int aa, int bb) -> F2 {
-      return sm[(((j - rn.lo) * NB + (bb - rb.lo)) * NA + (aa - ra.lo)) * nu + u];
-    };
-    const F2 hc = S(-1, a, b);
-    const double base = __ldg(cb + frame_vol(fr, -1, a, b) * U + u);
-    auto D = [&](int j, int aa, int bb) -> float {
-      const F2 x = S(j, aa, bb);
-      return __fadd_rn(__fsub_rn(x.hi, hc.hi), __fsub_rn(x.lo, hc.lo));
-    };
-    auto emit = [&](int ii, int e0, int e1, float incr) {
-      const double v = (ii == 1 && e0 == 0 && e1 == 0) ? base : add_back(hc, incr);
-      fb[frame_vol(fr, -1 - ii, 3 * a + e0 + cm.q0_off, 3 * b + e1 + cm.q1_off) * U] = v;
-    };
-    if (m == 3) taylor_interp_core<3, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
-    else if (m == 2) taylor_interp_core<2, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
-    else dlinear_interp_core<float>(D, emit, k, p, a, b);
+    // child (fine layer -1, tangential offsets 0, 0) of this centre and unknown
+    double* fc = fine + it.fine_offset + (int64_t)cm.slot * arr +
+                 frame_vol(fr, -1, 3 * a + cm.q0_off, 3 * b + cm.q1_off) * U + t.u0 + u;
+    const int ic = ((-1 - rn.lo) * NB + (b - rb.lo)) * NA * nu + (a - ra.lo) * nu + u;
+    auto S = [&](int j, int aa, int bb) -> SType { return sm[ic + (j + 1) * SJ + (bb - b) * SB + (aa - a) * SA]; };
+    auto store = [&](int ii, int e0, int e1, double v) { fc[-ii * gs_n + e0 * gs_a + e1 * gs_b] = v; };
+    if constexpr (SPLIT) {
+      const F2 hc = sm[ic];
+      const double base = __ldg(cb + frame_vol(fr, -1, a, b) * U + u);
+      auto D = [&](int j, int aa, int bb) -> float {
+        const F2 x = S(j, aa, bb);
+        return __fadd_rn(__fsub_rn(x.hi, hc.hi), __fsub_rn(x.lo, hc.lo));
+      };
+      auto emit = [&](int ii, int e0, int e1, float incr) {
+        double v;
+        if (ii == 1 && e0 == 0 && e1 == 0) v = base;
+        else if (e1 <= 0) v = __dadd_rn(base, f32_to_f64(incr));
+        else v = add_back(hc, incr);
+        store(ii, e0, e1, v);
+      };
+      if (m == 3) taylor_interp_core<3, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
+      else if (m == 2) taylor_interp_core<2, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
+      else dlinear_interp_core<float>(D, emit, k, p, a, b);
+    } else {
+      auto emit = [&](int ii, int e0, int e1, double v) { store(ii, e0, e1, v); };
+      if (m == 3) taylor_interp_core<3, double>(S, emit, c_wt_interp, k, p, a, b, S(-1, a, b));
+      else if (m == 2) taylor_interp_core<2, double>(S, emit, c_wt_interp, k, p, a, b, S(-1, a, b));
+      else dlinear_interp_core<double>(S, emit, k, p, a, b);
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Restriction tasks: one coarse halo column (a, b), one unknown.  F(i, da, db)
 // reads the fine volume at signed layer i, tangential offset (da, db) from the
-// column coincident with the coarse centre; C(j, v) writes coarse halo layer j.
+// fine column coincident with the coarse centre; C(j, v) writes coarse halo
+// layer j.
 // ---------------------------------------------------------------------------
-template <int M, bool SPLIT, typename Fine, typename Coarse>
-__device__ __forceinline__ void taylor_restrict_task(const Fine& F, const Coarse& C, int k) {
-  using T = typename Arith<SPLIT>::T;
-  // k >= 2 (checked on the host): coarse layer 0 coincides with fine layer 1
-  C(0, F(1, 0, 0));
-  if (k < 2) return;
-  int s, L;
-  stencil_window(k - 1, -k, k - 1, pure_exactness(M), s, L);
-  const double base = F(k - 1, 0, 0);
-  const T* wt = Arith<SPLIT>::wt_restrict();
-  const int pos = k - 1 - s;
-  T cf[M + 1];
+
+// Extrapolated coarse halo layer j of a Taylor restriction in split mode,
+// from the loaded window values v[0..L) (expansion value v[pos]): exact
+// float-pair differences, float-pair weighted sum, float64 rebuilt without
+// float64 instructions.
+__device__ __forceinline__ double pick5(const double* v, int idx) {
+  double r = v[0];
 #pragma unroll
-  for (int r = 1; r <= M; ++r) cf[r] = T(0);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    if (i < L) {
-      const double v = F(s + i, 0, 0);
-      const T dv = SPLIT ? (T)(v - base) : (T)v;
-#pragma unroll
-      for (int r = 1; r <= M; ++r) cf[r] += wt[wt_offset(L) + (pos * 3 + r - 1) * L + i] * dv;
-    }
-  }
-  for (int j = 1; j < k; ++j) {
-    const T e = T(3 * j + 2 - k);  // offset from fine layer k-1 to coarse layer j, units of h
-    T incr = cf[M];
-#pragma unroll
-    for (int r = M - 1; r >= 1; --r) incr = incr * e + cf[r];
-    incr *= e;
-    C(j, base + (double)incr);
-  }
+  for (int i = 1; i < 5; ++i) r = (i == idx) ? v[i] : r;
+  return r;
 }
 
+__device__ __forceinline__ double taylor_extrapolate_split(const double* v, int L, int pos, int m, int k, int j) {
+  const F2 b = split_f64(pick5(v, pos));
+  const int w0 = rw_index(m, k, j);
+  float ah = 0.f, al = 0.f;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    if (i < L && i != pos) {
+      const F2 x = split_f64(v[i]);
+      float e;
+      const float dh = two_sum(x.hi, -b.hi, e);
+      const float dl = __fadd_rn(e, __fsub_rn(x.lo, b.lo));
+      const float wh = c_rw_hi[w0 + i], wl = c_rw_lo[w0 + i];
+      const float pr = __fmul_rn(wh, dh);
+      float pe = __fmaf_rn(wh, dh, -pr);  // exact product error
+      pe = __fmaf_rn(wh, dl, pe);
+      pe = __fmaf_rn(wl, dh, pe);
+      float t;
+      ah = two_sum(ah, pr, t);
+      al = __fadd_rn(al, __fadd_rn(t, pe));
+    }
+  }
+  float e1, e2;
+  const float s1 = two_sum(b.hi, ah, e1);
+  const float tt = __fadd_rn(__fadd_rn(e1, b.lo), al);
+  const float s2 = fast_two_sum(s1, tt, e2);
+  return pair_to_f64(s2, e2);
+}
+
+// d-linear, float64: tangential 3x3 average per fine layer, least-squares
+// line along the normal.  All loads are issued before the arithmetic.
 template <typename Fine, typename Coarse>
-__device__ __forceinline__ void dlinear_restrict_task(const Fine& F, const Coarse& C, int k) {
+__device__ __forceinline__ void dlinear_restrict_f64(const Fine& F, const Coarse& C, int k) {
   const int nl = k == 1 ? 2 : k;
   double avg[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
     if (sl < nl) {
-      const int i = k == 1 ? sl - 1 : sl;
+      double v[9];  // one fine layer: all 9 loads before the sum
+#pragma unroll
+      for (int q = 0; q < 9; ++q) v[q] = F(k == 1 ? sl - 1 : sl, q % 3 - 1, q / 3 - 1);
       double acc = 0.0;
 #pragma unroll
-      for (int db = -1; db <= 1; ++db)
-#pragma unroll
-        for (int da = -1; da <= 1; ++da) acc += F(i, da, db);
+      for (int q = 0; q < 9; ++q) acc += v[q];
       avg[sl] = acc * (1.0 / 9.0);
     }
   }
   for (int j = 0; j < k; ++j) {
-    double v = 0.0;
+    double r = 0.0;
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl)
-      if (sl < nl) v += c_ls[ls_index(k, j, sl)] * avg[sl];
-    C(j, v);
+      if (sl < nl) r += c_ls[ls_index(k, j, sl)] * avg[sl];
+    C(j, r);
+  }
+}
+
+// d-linear, split: the same weights applied in float32 to exact float-pair
+// differences against the column's value in fine layer 0 (weights <= 10/3).
+template <typename Fine, typename Coarse>
+__device__ __forceinline__ void dlinear_restrict_split(const Fine& F, const Coarse& C, int k) {
+  const int nl = k == 1 ? 2 : k;
+  const F2 r = split_f64(F(0, 0, 0));  // fine layer 0, centre column
+  float avg[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    if (sl < nl) {
+      double v[9];  // one fine layer: all 9 loads before the arithmetic
+#pragma unroll
+      for (int q = 0; q < 9; ++q) v[q] = F(k == 1 ? sl - 1 : sl, q % 3 - 1, q / 3 - 1);
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const F2 x = split_f64(v[q]);
+        acc += __fadd_rn(__fsub_rn(x.hi, r.hi), __fsub_rn(x.lo, r.lo));
+      }
+      avg[sl] = acc * (1.0f / 9.0f);
+    }
+  }
+  for (int j = 0; j < k; ++j) {
+    float w = 0.f;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl)
+      if (sl < nl) w += c_ls_f[ls_index(k, j, sl)] * avg[sl];
+    C(j, add_back(r, w));
   }
 }
 
@@ -459,27 +515,78 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
   const int p = it.patch_size, k = it.overlap, m = it.order;
   const FaceFrame fr = face_frame(it.face, p, k);
   const int64_t arr = fr.vols * U;
-  const double* fb = fine + it.fine_offset + (int64_t)t.slot * arr + t.u0;
+  const int gs_n = (int)fr.s_n * U, gs_a = (int)fr.s_t0 * U, gs_b = (int)fr.s_t1 * U;
   double* cb = coarse + it.coarse_offset + t.u0;
-  const int s0 = t.sub % 3, s1 = t.sub / 3;
+  const float inv_w = 3.0f / (float)p;
   const int nu = t.nu;
   const int ntask = t.na * t.nb * nu;
-  for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
-    const int u = e % nu;
-    const int ci = e / nu;
-    const int a = t.a0 + ci % t.na, b = t.b0 + ci / t.na;
+  // fine column (layer 0) and coarse halo column (layer 0) of a task
+  auto columns = [&](const Counter4& c, const double*& fcol, double*& ccol) {
+    const int u = c.u, a = t.a0 + c.x, b = t.b0 + c.y;
+    int s0, s1, slot;
+    if (t.sub >= 0) {
+      s0 = t.sub % 3; s1 = t.sub / 3; slot = t.slot;
+    } else {  // whole-face tile: (a + 1/2) / w is never within 1/32 of an integer
+      s0 = (int)(((float)a + 0.5f) * inv_w);
+      s1 = (int)(((float)b + 0.5f) * inv_w);
+      slot = s0 + 3 * s1;
+    }
     const int q0 = 3 * a + 1 - s0 * p, q1 = 3 * b + 1 - s1 * p;
-    auto F = [&](int i, int da, int db) -> double {
-      return __ldg(fb + frame_vol(fr, i, q0 + da, q1 + db) * U + u);
-    };
-    auto C = [&](int j, double v) { cb[frame_vol(fr, j, a, b) * U + u] = v; };
-    // Restriction extrapolates up to (3k-1-(k-1))h = 5h away (k = 3), which
-    // multiplies float32 rounding by up to ~125 (Taylor-3): it stays float64
-    // in both precision modes.
-    (void)SPLIT;
-    if (m == 3) taylor_restrict_task<3, false>(F, C, k);
-    else if (m == 2) taylor_restrict_task<2, false>(F, C, k);
-    else dlinear_restrict_task(F, C, k);
+    fcol = fine + it.fine_offset + (int64_t)slot * arr + t.u0 + frame_vol(fr, 0, q0, q1) * U + u;
+    ccol = cb + frame_vol(fr, 0, a, b) * U + u;
+  };
+  Counter4 c;
+  c.init(threadIdx.x, blockDim.x, nu, t.na, t.nb);
+  if (m >= 2) {
+    // Taylor: the derivative window about fine layer k-1 holds fine layer 1
+    // (the injection source); two columns per iteration keep 2 x L loads in
+    // flight per thread.
+    int s, L;
+    stencil_window(k - 1, -k, k - 1, pure_exactness(m), s, L);
+    const int pos = k - 1 - s;
+    constexpr int R = 2;
+    for (int e0 = threadIdx.x; e0 < ntask; e0 += R * blockDim.x) {
+      double v[R][5];
+      double* ccol[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const double* fcol;
+        columns(c, fcol, ccol[r]);
+        const bool ok = e0 + r * (int)blockDim.x < ntask;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) v[r][i] = (ok && i < L) ? __ldg(fcol + (s + i) * gs_n) : 0.0;
+        if (!ok) ccol[r] = nullptr;
+        c.advance(nu, t.na, t.nb);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!ccol[r]) continue;
+        ccol[r][0] = pick5(v[r], 1 - s);  // layer 0 coincides with fine layer 1
+        for (int j = 1; j < k; ++j) {
+          double out;
+          if (SPLIT) {
+            out = taylor_extrapolate_split(v[r], L, pos, m, k, j);
+          } else {
+            const double* w = c_rw + rw_index(m, k, j);
+            double acc = 0.0;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) acc = fma(w[i], v[r][i], acc);
+            out = acc;
+          }
+          ccol[r][j * gs_n] = out;
+        }
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < ntask; e += blockDim.x, c.advance(nu, t.na, t.nb)) {
+      const double* fcol;
+      double* ccol;
+      columns(c, fcol, ccol);
+      auto F = [&](int i, int da, int db) -> double { return __ldg(fcol + i * gs_n + da * gs_a + db * gs_b); };
+      auto C = [&](int j, double v) { ccol[j * gs_n] = v; };
+      if (SPLIT) dlinear_restrict_split(F, C, k);
+      else dlinear_restrict_f64(F, C, k);
+    }
   }
 }
 
