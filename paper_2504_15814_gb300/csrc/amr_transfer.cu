@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "builder.hpp"
+#include "adjoint_kernels.cuh"
 #include "transfer_kernels.cuh"
 
 namespace {
@@ -82,14 +83,55 @@ struct amr_transfer_plan {
   int n_itiles = 0, n_rtiles = 0;
   int interp_smem = 0;  // bytes of dynamic shared memory per interpolation CTA
   amr_transfer_plan_info info{};
+  // adjoint tables, built on the first adjoint call
+  std::vector<amr_transfer_item> items_h;
+  bool adj_ready = false;
+  int n_pt_tiles = 0, n_rt_tiles = 0;
+  amr::AdjointTile *pt_tiles_d = nullptr, *rt_tiles_d = nullptr;
+  int32_t *group_ptr_d = nullptr, *group_items_d = nullptr, *item_class_d = nullptr;
+  int32_t *cls_pt_rows_d = nullptr, *cls_rt_rows_d = nullptr, *pt_row_ptr_d = nullptr, *rt_row_ptr_d = nullptr;
+  uint32_t *pt_col_d = nullptr, *rt_col_d = nullptr;
+  double *pt_val_d = nullptr, *rt_val_d = nullptr;
 };
 
 static void free_plan(amr_transfer_plan* p) {
   if (!p) return;
-  cudaFree(p->items_d);
-  cudaFree(p->itiles_d);
-  cudaFree(p->rtiles_d);
+  void* ptrs[] = {p->items_d, p->itiles_d, p->rtiles_d, p->pt_tiles_d, p->rt_tiles_d, p->group_ptr_d,
+                  p->group_items_d, p->item_class_d, p->cls_pt_rows_d, p->cls_rt_rows_d, p->pt_row_ptr_d,
+                  p->rt_row_ptr_d, p->pt_col_d, p->rt_col_d, p->pt_val_d, p->rt_val_d};
+  for (void* q : ptrs) cudaFree(q);
   delete p;
+}
+
+// Build and upload the transposed operators (synchronous; first adjoint call).
+static amr_status ensure_adjoint(amr_transfer_plan* p) {
+  if (p->adj_ready) return AMR_OK;
+  amr_transfer_desc d{};
+  d.abi_version = AMR_TRANSFER_ABI_VERSION;
+  d.num_unknowns = p->U;
+  d.num_items = (int64_t)p->items_h.size();
+  d.items = p->items_h.data();
+  amr::AdjointBuild ab;
+  try {
+    ab = amr::build_adjoint(d);
+  } catch (const std::bad_alloc&) {
+    return AMR_ERR_OUT_OF_MEMORY;
+  }
+  amr_status st;
+  if ((st = upload(ab.pt_tiles, &p->pt_tiles_d)) != AMR_OK || (st = upload(ab.rt_tiles, &p->rt_tiles_d)) != AMR_OK ||
+      (st = upload(ab.group_ptr, &p->group_ptr_d)) != AMR_OK ||
+      (st = upload(ab.group_items, &p->group_items_d)) != AMR_OK ||
+      (st = upload(ab.item_class, &p->item_class_d)) != AMR_OK ||
+      (st = upload(ab.cls_pt_rows, &p->cls_pt_rows_d)) != AMR_OK ||
+      (st = upload(ab.cls_rt_rows, &p->cls_rt_rows_d)) != AMR_OK ||
+      (st = upload(ab.pt.row_ptr, &p->pt_row_ptr_d)) != AMR_OK || (st = upload(ab.pt.col, &p->pt_col_d)) != AMR_OK ||
+      (st = upload(ab.pt.val, &p->pt_val_d)) != AMR_OK || (st = upload(ab.rt.row_ptr, &p->rt_row_ptr_d)) != AMR_OK ||
+      (st = upload(ab.rt.col, &p->rt_col_d)) != AMR_OK || (st = upload(ab.rt.val, &p->rt_val_d)) != AMR_OK)
+    return st;
+  p->n_pt_tiles = (int)ab.pt_tiles.size();
+  p->n_rt_tiles = (int)ab.rt_tiles.size();
+  p->adj_ready = true;
+  return AMR_OK;
 }
 
 extern "C" {
@@ -137,8 +179,8 @@ amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_
   p->precision = desc->precision;
   p->coarse_elems = desc->coarse_elems;
   p->fine_elems = desc->fine_elems;
-  std::vector<amr_transfer_item> items(desc->items, desc->items + desc->num_items);
-  if ((st = upload(items, &p->items_d)) != AMR_OK ||
+  p->items_h.assign(desc->items, desc->items + desc->num_items);
+  if ((st = upload(p->items_h, &p->items_d)) != AMR_OK ||
       (st = upload(br.interp_tiles, &p->itiles_d)) != AMR_OK ||
       (st = upload(br.restrict_tiles, &p->rtiles_d)) != AMR_OK) {
     free_plan(p);
@@ -203,14 +245,34 @@ amr_status amr_transfer_plan_restrict(amr_transfer_plan* p, const double* fine, 
 
 amr_status amr_transfer_plan_interpolate_adjoint(amr_transfer_plan* p, const double* g_fine, double* g_coarse,
                                                  void* stream) {
-  (void)p; (void)g_fine; (void)g_coarse; (void)stream;
-  return AMR_ERR_UNSUPPORTED;
+  amr_status st = check_call(p, g_fine, p ? p->fine_elems : 0, g_coarse, p ? p->coarse_elems : 0);
+  if (st != AMR_OK) return st;
+  if ((st = ensure_adjoint(p)) != AMR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->coarse_elems > 0) AMR_CUDA(cudaMemsetAsync(g_coarse, 0, (size_t)p->coarse_elems * 8, s));
+  if (p->n_pt_tiles > 0) {
+    amr::interp_adjoint_kernel<<<p->n_pt_tiles, kThreads, 0, s>>>(
+        p->items_d, p->pt_tiles_d, p->group_ptr_d, p->group_items_d, p->item_class_d, p->cls_pt_rows_d,
+        p->pt_row_ptr_d, p->pt_col_d, p->pt_val_d, p->U, g_fine, g_coarse);
+    AMR_CUDA(cudaGetLastError());
+  }
+  return AMR_OK;
 }
 
 amr_status amr_transfer_plan_restrict_adjoint(amr_transfer_plan* p, const double* g_coarse, double* g_fine,
                                               void* stream) {
-  (void)p; (void)g_coarse; (void)g_fine; (void)stream;
-  return AMR_ERR_UNSUPPORTED;
+  amr_status st = check_call(p, g_coarse, p ? p->coarse_elems : 0, g_fine, p ? p->fine_elems : 0);
+  if (st != AMR_OK) return st;
+  if ((st = ensure_adjoint(p)) != AMR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->fine_elems > 0) AMR_CUDA(cudaMemsetAsync(g_fine, 0, (size_t)p->fine_elems * 8, s));
+  if (p->n_rt_tiles > 0) {
+    amr::restrict_adjoint_kernel<<<p->n_rt_tiles, kThreads, 0, s>>>(p->items_d, p->rt_tiles_d, p->cls_rt_rows_d,
+                                                                    p->rt_row_ptr_d, p->rt_col_d, p->rt_val_d, p->U,
+                                                                    g_coarse, g_fine);
+    AMR_CUDA(cudaGetLastError());
+  }
+  return AMR_OK;
 }
 
 amr_status amr_transfer_plan_get_info(const amr_transfer_plan* p, amr_transfer_plan_info* info) {

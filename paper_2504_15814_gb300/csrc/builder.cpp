@@ -328,3 +328,195 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
 }
 
 }  // namespace amr
+
+// ---------------------------------------------------------------------------
+// Explicit operator rows and their transposes (adjoint).
+// ---------------------------------------------------------------------------
+namespace amr {
+namespace {
+
+using Row = std::map<uint32_t, double>;
+
+// 1-D stencil of derivative order r (0 = point evaluation) about c on
+// [lo, hi] with exactness degree E: (index, weight) pairs from a table of
+// Taylor-coefficient weights.
+std::vector<std::pair<int, double>> axis_stencil(const double* wt, int c, int lo, int hi, int E, int r) {
+  if (r == 0) return {{c, 1.0}};
+  int s, L;
+  stencil_window(c, lo, hi, E, s, L);
+  std::vector<std::pair<int, double>> out;
+  for (int i = 0; i < L; ++i) {
+    const double w = wt[wt_offset(L) + ((c - s) * 3 + r - 1) * L + i];
+    if (w != 0.0) out.push_back({s + i, w});
+  }
+  return out;
+}
+
+void add_taylor_interp_row(Row& row, int p, int k, int order, int a, int b, int en, int e0, int e1) {
+  const double* wt = tables().wt_interp;
+  for (int x = 0; x <= order; ++x)
+    for (int y = 0; x + y <= order; ++y)
+      for (int z = 0; x + y + z <= order; ++z) {
+        double coeff = 1.0;
+        for (int q = 0; q < x; ++q) coeff *= en;
+        for (int q = 0; q < y; ++q) coeff *= e0;
+        for (int q = 0; q < z; ++q) coeff *= e1;
+        if (coeff == 0.0) continue;
+        const int nz = (x > 0) + (y > 0) + (z > 0);
+        const int E = nz <= 1 ? pure_exactness(order) : mixed_exactness(order);
+        const auto sn = axis_stencil(wt, -1, -k, k - 1, E, x);
+        const auto s0 = axis_stencil(wt, a, 0, p - 1, E, y);
+        const auto s1 = axis_stencil(wt, b, 0, p - 1, E, z);
+        for (auto& [jn, wn] : sn)
+          for (auto& [ja, wa] : s0)
+            for (auto& [jb, wb] : s1) row[pack_vol(0, jn + k, jb, ja)] += coeff * wn * wa * wb;
+      }
+}
+
+// d-linear weights along one axis for child offset e in {-1, 0, 1} about
+// coarse index c with neighbours available on [0, n-1].
+std::vector<std::pair<int, double>> dlin_axis(int c, int n, int e) {
+  if (e == 0) return {{c, 1.0}};
+  if (e < 0) {
+    if (c > 0) return {{c - 1, 1.0 / 3.0}, {c, 2.0 / 3.0}};
+    return {{c, 4.0 / 3.0}, {c + 1, -1.0 / 3.0}};
+  }
+  if (c < n - 1) return {{c, 2.0 / 3.0}, {c + 1, 1.0 / 3.0}};
+  return {{c - 1, -1.0 / 3.0}, {c, 4.0 / 3.0}};
+}
+
+}  // namespace
+
+Rows interpolation_rows(int sub, int slot, int p, int k, int order) {
+  Rows r;
+  const int s0 = sub % 3, s1 = sub / 3;
+  for (int i = -k; i <= -1; ++i)
+    for (int q1 = 0; q1 < p; ++q1)
+      for (int q0 = 0; q0 < p; ++q0) {
+        const int g0 = s0 * p + q0, g1 = s1 * p + q1;
+        const int a = g0 / 3, b = g1 / 3;
+        const int e0 = g0 - 3 * a - 1, e1 = g1 - 3 * b - 1, en = i + 2;
+        Row row;
+        if (order == AMR_ORDER_DLINEAR) {
+          std::vector<std::pair<int, double>> wn;
+          if (en == 1) wn = {{-1, 2.0 / 3.0}, {0, 1.0 / 3.0}};
+          else if (en == 0) wn = {{-1, 1.0}};
+          else wn = {{-2, 1.0 / 3.0}, {-1, 2.0 / 3.0}};
+          for (auto& [jn, w_n] : wn)
+            for (auto& [ja, w_a] : dlin_axis(a, p, e0))
+              for (auto& [jb, w_b] : dlin_axis(b, p, e1)) row[pack_vol(0, jn + k, jb, ja)] += w_n * w_a * w_b;
+        } else {
+          add_taylor_interp_row(row, p, k, order, a, b, en, e0, e1);
+        }
+        r.out_vol.push_back(pack_vol(slot, i + k, q1, q0));
+        r.rows.emplace_back(row.begin(), row.end());
+      }
+  return r;
+}
+
+Rows restriction_rows(int sub, int slot, int p, int k, int order) {
+  Rows r;
+  const Tables& t = tables();
+  const int s0 = sub % 3, s1 = sub / 3, w = p / 3;
+  for (int j = 0; j < k; ++j)
+    for (int b = s1 * w; b < (s1 + 1) * w; ++b)
+      for (int a = s0 * w; a < (s0 + 1) * w; ++a) {
+        const int q0 = 3 * a + 1 - s0 * p, q1 = 3 * b + 1 - s1 * p;
+        Row row;
+        if (order == AMR_ORDER_DLINEAR) {
+          const int nl = k == 1 ? 2 : k;
+          for (int sl = 0; sl < nl; ++sl) {
+            const int i = k == 1 ? sl - 1 : sl;
+            const double wl = t.ls[ls_index(k, j, sl)] / 9.0;
+            for (int db = -1; db <= 1; ++db)
+              for (int da = -1; da <= 1; ++da) row[pack_vol(slot, i + k, q1 + db, q0 + da)] += wl;
+          }
+        } else if (j == 0) {
+          row[pack_vol(slot, 1 + k, q1, q0)] = 1.0;
+        } else {
+          int s, L;
+          stencil_window(k - 1, -k, k - 1, pure_exactness(order), s, L);
+          for (int i = 0; i < L; ++i) {
+            const double wv = t.rw[rw_index(order, k, j) + i];
+            if (wv != 0.0) row[pack_vol(slot, s + i + k, q1, q0)] += wv;
+          }
+        }
+        r.out_vol.push_back(pack_vol(0, j + k, b, a));
+        r.rows.emplace_back(row.begin(), row.end());
+      }
+  return r;
+}
+
+namespace {
+
+// Row index of a packed volume in a CSR over nslot face arrays of 2k p^2 volumes.
+int row_of(uint32_t v, int p, int k) {
+  const int slot = (int)(v >> 15), lk = (int)((v >> 12) & 7), q1 = (int)((v >> 6) & 63), q0 = (int)(v & 63);
+  return ((slot * 2 * k + lk) * p + q1) * p + q0;
+}
+
+void append_transpose(CsrT& out, std::vector<int32_t>& cls_rows, const std::vector<Rows>& blocks, int nrows, int p,
+                      int k) {
+  std::vector<std::vector<std::pair<uint32_t, double>>> t(nrows);
+  for (const Rows& blk : blocks)
+    for (size_t i = 0; i < blk.rows.size(); ++i)
+      for (auto& [in_vol, w] : blk.rows[i]) t[row_of(in_vol, p, k)].push_back({blk.out_vol[i], w});
+  cls_rows.push_back((int32_t)out.row_ptr.size());
+  for (int r = 0; r < nrows; ++r) {
+    out.row_ptr.push_back((int32_t)out.col.size());
+    for (auto& [c, w] : t[r]) {
+      out.col.push_back(c);
+      out.val.push_back(w);
+    }
+  }
+  out.row_ptr.push_back((int32_t)out.col.size());
+}
+
+}  // namespace
+
+AdjointBuild build_adjoint(const amr_transfer_desc& desc) {
+  AdjointBuild ab;
+  const int64_t U = desc.num_unknowns;
+  std::map<std::tuple<int, int, int, int>, int> classes;
+  std::map<int64_t, std::vector<int32_t>> groups;
+  for (int64_t it = 0; it < desc.num_items; ++it) {
+    const amr_transfer_item& x = desc.items[it];
+    auto key = std::make_tuple(x.patch_size, x.overlap, x.order, x.subface);
+    auto f = classes.find(key);
+    if (f == classes.end()) {
+      const int id = (int)classes.size();
+      f = classes.emplace(key, id).first;
+      const int p = x.patch_size, k = x.overlap, m = x.order;
+      std::vector<Rows> pblocks, rblocks;
+      const int nsub = x.subface < 0 ? 9 : 1;
+      for (int sl = 0; sl < nsub; ++sl) {
+        const int sub = x.subface < 0 ? sl : x.subface;
+        pblocks.push_back(interpolation_rows(sub, sl, p, k, m));
+        rblocks.push_back(restriction_rows(sub, sl, p, k, m));
+      }
+      const int arr = 2 * k * p * p;
+      append_transpose(ab.pt, ab.cls_pt_rows, pblocks, arr, p, k);
+      append_transpose(ab.rt, ab.cls_rt_rows, rblocks, nsub * arr, p, k);
+    }
+    ab.item_class.push_back(f->second);
+    groups[x.coarse_offset].push_back((int32_t)it);
+  }
+  ab.group_ptr.push_back(0);
+  for (auto& [off, members] : groups) {
+    const int32_t g = (int32_t)ab.group_ptr.size() - 1;
+    for (int32_t m : members) ab.group_items.push_back(m);
+    ab.group_ptr.push_back((int32_t)ab.group_items.size());
+    for (int64_t u0 = 0; u0 < U; u0 += 128)
+      ab.pt_tiles.push_back({g, 0, 0, (int16_t)u0, (int16_t)std::min<int64_t>(128, U - u0)});
+  }
+  for (int64_t it = 0; it < desc.num_items; ++it) {
+    const int nsub = desc.items[it].subface < 0 ? 9 : 1;
+    for (int sl = 0; sl < nsub; ++sl)
+      for (int64_t u0 = 0; u0 < U; u0 += 128)
+        ab.rt_tiles.push_back({(int32_t)it, (int16_t)sl, (int16_t)ab.item_class[it], (int16_t)u0,
+                               (int16_t)std::min<int64_t>(128, U - u0)});
+  }
+  return ab;
+}
+
+}  // namespace amr

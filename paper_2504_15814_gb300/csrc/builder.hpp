@@ -31,15 +31,31 @@ struct Tables {
 // Built once per process.
 const Tables& tables();
 
-// Sparse transposed operator of one face class, in the reference frame.
-// Row r = reference volume of the operator's input face array
-//   (j + k) * p * p + b * p + a;
-// column = slot * (2 k p^2) + reference volume of the output face array.
+// Packed reference-frame volume of a face array: signed normal layer l
+// (stored as l + k, 3 bits), tangential q1 and q0 (6 bits each), and the
+// index of the fine face array within the item (4 bits).
+__host__ __device__ inline uint32_t pack_vol(int slot, int layer_plus_k, int q1, int q0) {
+  return ((uint32_t)slot << 15) | ((uint32_t)layer_plus_k << 12) | ((uint32_t)q1 << 6) | (uint32_t)q0;
+}
+
+// Transposed operator (P^T or R^T) of one face class in CSR form.  Row r is
+// the reference volume (l + k) p^2 + q1 p + q0 of the adjoint's output face
+// array (the coarse array for P^T, the fine array of one subface for R^T);
+// entries are packed volumes of the adjoint's input and their weights.
 struct CsrT {
-  std::vector<int32_t> row_ptr;  // rows + 1
-  std::vector<int32_t> col;
+  std::vector<int32_t> row_ptr;
+  std::vector<uint32_t> col;
   std::vector<double> val;
 };
+
+// Explicit operator rows of one subface in the reference frame:
+// out_vol[i] (packed) <- sum_e w_e in_vol[e] (packed).
+struct Rows {
+  std::vector<uint32_t> out_vol;
+  std::vector<std::vector<std::pair<uint32_t, double>>> rows;
+};
+Rows interpolation_rows(int sub, int slot, int p, int k, int order);
+Rows restriction_rows(int sub, int slot, int p, int k, int order);
 
 struct BuildResult {
   amr_status status = AMR_OK;
@@ -52,14 +68,22 @@ struct BuildResult {
 
 BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget);
 
-// Explicit operator rows of P (interpolation) or R (restriction) for one
-// subface, in the reference frame: out_vol[i] is the reference volume of the
-// output face array, rows[i] the (input reference volume, weight) pairs.
-struct Rows {
-  std::vector<int32_t> out_vol;
-  std::vector<std::vector<std::pair<int32_t, double>>> rows;
+// Adjoint work: P^T over coarse face arrays (items sharing one coarse array
+// form a group and are summed in item order), R^T over each item's fine
+// face arrays.  Classes are (p, k, order, subface) with subface -1 for a whole
+// hanging face.
+struct AdjointTile {
+  int32_t index;  // group (P^T) or item (R^T)
+  int16_t slot;   // fine face array within the item (R^T)
+  int16_t klass;  // class of the item (R^T)
+  int16_t u0, nu;
 };
-Rows interpolation_rows(int sub, int p, int k, int order);
-Rows restriction_rows(int sub, int p, int k, int order);
+struct AdjointBuild {
+  std::vector<int32_t> group_ptr, group_items, item_class;
+  std::vector<AdjointTile> pt_tiles, rt_tiles;
+  std::vector<int32_t> cls_pt_rows, cls_rt_rows;  // offset of each class's row_ptr in the concatenation
+  CsrT pt, rt;                                    // concatenated classes (row_ptr absolute into col/val)
+};
+AdjointBuild build_adjoint(const amr_transfer_desc& desc);
 
 }  // namespace amr
