@@ -281,11 +281,134 @@ def main():
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "32 hanging faces of the batch, Taylor-3 interpolate+restrict, "
                                           "operators prebuilt, scipy CSR apply (single thread)"}
+        line["workloads"] = other_workloads(B, wl, stream)
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _time_steps(step, n, stream):
+    import torch
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def other_workloads(B, wl, stream):
+    """The other synthetic workloads of the benchmark family, measured on the
+    same GPU: single face (launch latency, direct vs captured graph), uneven
+    batch (default vs autotuned launch shapes), split precision on puncture
+    fields (error against the FP64 oracle per field class), adjoint."""
+    import numpy as np
+    import torch
+    from oracle import transfer as tr
+    out = {}
+    # single face: p = 6, k = 3, U = 1, Taylor-2, random quadratic on the unit cube
+    items, cl, fl = wl.make_items([0], [-1], [6], [3], [2], 1)
+    rng = np.random.Generator(np.random.PCG64(wl.SEED_BASE + 0))
+    coef = torch.as_tensor(rng.uniform(-1, 1, 10))
+    H = 1.0 / 6
+
+    def quad(x):
+        x = x * H
+        t = torch.stack([torch.ones_like(x[:, 0]), x[:, 0], x[:, 1], x[:, 2], x[:, 0] ** 2, x[:, 1] ** 2,
+                         x[:, 2] ** 2, x[:, 0] * x[:, 1], x[:, 0] * x[:, 2], x[:, 1] * x[:, 2]], 1)
+        return (t @ coef.to(x.device))[:, None]
+
+    c, f = wl.polynomial_buffers(items, 1, cl, fl, quad, origins=np.array([[1.0 / H, 0.0, 0.0]]), device="cuda")
+    co = c.clone()
+    exact_f, exact_c = f.clone(), c.clone()
+    plan = B.Plan(items, 1, cl, fl, B.PREC_FP64)
+    direct = _time_steps(lambda: (plan.interpolate(c, f), plan.restrict(f, co)), 200, stream)
+    plan.capture_step(c, f, co)
+    graph = _time_steps(lambda: plan.launch_step(), 200, stream)
+    torch.cuda.synchronize()
+    err = max(float((f - exact_f).abs().max() / exact_f.abs().max()), float((co - exact_c).abs().max() / exact_c.abs().max()))
+    outs = (plan.info["interp_outputs"] + plan.info["restrict_outputs"])
+    out["single_face"] = {"workload": "1 hanging face, p=6, k=3, U=1, Taylor-2, quadratic field",
+                          "us_per_step_direct": direct * 1e3, "us_per_step_graph": graph * 1e3,
+                          "volume_unknowns_per_step": outs, "max_rel_err_vs_exact_quadratic": err,
+                          "launches_per_step": 2}
+    plan.close()
+    # uneven batch: 20,000 subface items, p in {6,9,12}, k in {2,3}, orders 1/2/3
+    items, coarse, fine = wl.uneven_batch(device="cuda")
+    U = 59
+    co = coarse.clone()
+    for prec_name, prec in (("split", B.PREC_SPLIT), ("fp64", B.PREC_FP64)):
+        plan = B.Plan(items, U, coarse.numel(), fine.numel(), prec)
+        info = plan.info
+        outs = (info["interp_outputs"] + info["restrict_outputs"]) * U
+        t_default = _time_steps(lambda: (plan.interpolate(coarse, fine), plan.restrict(fine, co)), 10, stream)
+        chosen = plan.autotune(coarse, fine, co)
+        t_tuned = _time_steps(lambda: (plan.interpolate(coarse, fine), plan.restrict(fine, co)), 10, stream)
+        plan.capture_step(coarse, fine, co)
+        t_graph = _time_steps(lambda: plan.launch_step(), 10, stream)
+        out[f"uneven_batch_{prec_name}"] = {
+            "workload": "20,000 subface items, p 6/9/12 (40/40/20 %), k 2/3, orders 1/2/3, U=59",
+            "ms_per_step_default": t_default, "ms_per_step_autotuned": t_tuned, "ms_per_step_graph": t_graph,
+            "autotuned": chosen, "value": outs / (min(t_tuned, t_graph) * 1e-3), "unit": UNIT,
+            "step_gbs": (info["interp_bytes"] + info["restrict_bytes"]) / (min(t_tuned, t_graph) * 1e-3) / 1e9}
+        plan.close()
+    del items, coarse, fine, co
+    torch.cuda.empty_cache()
+    # split precision on puncture-like fields: 8,192 faces, Taylor-3
+    items, coarse, fine = wl.puncture_batch(device="cuda")
+    co = coarse.clone()
+    res = {"workload": "8,192 hanging faces, p=9, k=3, U=59, Taylor-3, puncture-like fields"}
+    for prec_name, prec in (("split", B.PREC_SPLIT), ("fp64", B.PREC_FP64)):
+        plan = B.Plan(items, U, coarse.numel(), fine.numel(), prec)
+        info = plan.info
+        fo = fine.clone()
+        t = _time_steps(lambda: (plan.interpolate(coarse, fo), plan.restrict(fine, co)), 5, stream)
+        res[f"{prec_name}_ms_per_step"] = t
+        res[f"{prec_name}_value"] = (info["interp_outputs"] + info["restrict_outputs"]) * U / (t * 1e-3)
+        # error against the FP64 oracle per field class (u mod 3) on 8 sampled faces
+        arr = 2 * K * P * P * U
+        errs = {0: [], 1: [], 2: []}
+        rng = np.random.default_rng(8)
+        for i in rng.choice(len(items), 8, replace=False):
+            it = items[int(i)].copy()
+            c0, f0 = int(it["coarse_offset"]), int(it["fine_offset"])
+            one = np.array([it])
+            one["coarse_offset"], one["fine_offset"] = 0, 0
+            ch, fh = coarse[c0:c0 + arr].cpu().numpy(), fine[f0:f0 + 9 * arr].cpu().numpy()
+            for got, ref in ((fo[f0:f0 + 9 * arr].cpu().numpy(), tr.interpolate(one, U, ch, fh)),
+                             (co[c0:c0 + arr].cpu().numpy(), tr.restrict(one, U, fh, ch))):
+                g2, r2 = got.reshape(-1, U), ref.reshape(-1, U)
+                e = np.abs(g2 - r2).max(axis=0) / np.maximum(np.abs(r2).max(axis=0), 1e-300)
+                for u in range(U):
+                    errs[u % 3].append(e[u])
+        names = {0: "psi", 1: "lapse", 2: "shift"}
+        res[f"{prec_name}_err_vs_fp64"] = {names[q]: {"max": float(np.max(v)), "rms": float(np.sqrt(np.mean(np.square(v))))}
+                                           for q, v in errs.items()}
+        plan.close()
+        del fo
+    out["puncture_split"] = res
+    del items, coarse, fine, co
+    torch.cuda.empty_cache()
+    # adjoint: 4,096 faces, Taylor-3, P^T and R^T
+    items, coarse, fine = wl.uniform_batch(n_faces=4096, U=U, order=3, config_index=4, device="cuda")
+    plan = B.Plan(items, U, coarse.numel(), fine.numel(), B.PREC_FP64)
+    gc, gf = torch.empty_like(coarse), torch.empty_like(fine)
+    plan.interpolate_adjoint(fine, gc)  # builds the transposed tables
+    t = _time_steps(lambda: (plan.interpolate_adjoint(fine, gc), plan.restrict_adjoint(coarse, gf)), 5, stream)
+    info = plan.info
+    out["adjoint"] = {"workload": "4,096 hanging faces, p=9, k=3, U=59, Taylor-3, P^T + R^T (float64)",
+                      "ms_per_step": t, "value": (coarse.numel() + fine.numel()) / (t * 1e-3),
+                      "unit": "gradient entries/s"}
+    plan.close()
+    del items, coarse, fine, gc, gf
+    torch.cuda.empty_cache()
+    return out
 
 
 def compare_paths(B, wl, items, coarse, fine, coarse_out, U, args, stream, plan_main):

@@ -120,7 +120,9 @@ amr_status amr_transfer_plan_restrict(amr_transfer_plan* plan, const double* fin
 /* g_coarse = P^T g_fine over the whole coarse buffer: overwrites all
  * coarse_elems values (zero where no weight reaches) and sums the
  * contributions of items that share a coarse face array.  Only the ghost
- * entries of g_fine are read.  Always float64. */
+ * entries of g_fine are read.  Always float64.  The first adjoint call on a
+ * plan builds its transposed-operator tables (host work and a synchronous
+ * upload): make it before capturing a stream. */
 amr_status amr_transfer_plan_interpolate_adjoint(amr_transfer_plan* plan, const double* g_fine,
                                                  double* g_coarse, void* cuda_stream);
 
@@ -143,6 +145,43 @@ typedef struct {
 } amr_transfer_plan_info;
 
 amr_status amr_transfer_plan_get_info(const amr_transfer_plan* plan, amr_transfer_plan_info* info);
+
+/* Launch shapes of a plan.  interp_threads / restrict_threads: CTA size of
+ * the two kernels (32..256, a multiple of 32); interp_smem_budget: bytes of
+ * shared memory an interpolation tile may stage (4096..200704; it sets how
+ * many unknowns one tile carries). */
+typedef struct {
+  int32_t interp_threads;
+  int32_t interp_smem_budget;
+  int32_t restrict_threads;
+  int32_t reserved; /* 0 */
+} amr_transfer_tuning;
+
+amr_status amr_transfer_plan_get_tuning(const amr_transfer_plan* plan, amr_transfer_tuning* out);
+
+/* Rebuild the plan's tiles for these launch shapes (synchronous).  Drops a
+ * captured step graph. */
+amr_status amr_transfer_plan_set_tuning(amr_transfer_plan* plan, const amr_transfer_tuning* tuning);
+
+/* Autotuner: times candidate launch shapes of interpolate and restrict on the
+ * caller's buffers (CUDA events on the stream; synchronises it), keeps the
+ * fastest, and reports it in *chosen (may be NULL).  fine's ghost halves and
+ * coarse_out's restricted halo volumes are overwritten with valid results;
+ * coarse_out may equal coarse.  Drops a captured step graph. */
+amr_status amr_transfer_plan_autotune(amr_transfer_plan* plan, const double* coarse, double* fine,
+                                      double* coarse_out, void* cuda_stream, amr_transfer_tuning* chosen);
+
+/* Capture one transfer step -- interpolate(coarse -> fine) followed by
+ * restrict(fine -> coarse_out) -- into a CUDA graph owned by the plan, for
+ * these fixed buffers (replaces a previous capture).  Nothing runs until
+ * amr_transfer_plan_launch_step.  Not to be called while the caller's
+ * stream is itself being captured. */
+amr_status amr_transfer_plan_capture_step(amr_transfer_plan* plan, const double* coarse, double* fine,
+                                          double* coarse_out);
+
+/* Enqueue the captured step graph on a stream (AMR_ERR_INVALID_ARGUMENT if
+ * none is captured). */
+amr_status amr_transfer_plan_launch_step(amr_transfer_plan* plan, void* cuda_stream);
 
 /* Release the plan's device tables (synchronises its device).  NULL is a no-op. */
 amr_status amr_transfer_plan_destroy(amr_transfer_plan* plan);

@@ -45,6 +45,11 @@ class PlanInfo(ctypes.Structure):
                 ("restrict_launches", ctypes.c_int32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("interp_threads", ctypes.c_int32), ("interp_smem_budget", ctypes.c_int32),
+                ("restrict_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 ENTRY_POINTS = {
     "amr_transfer_plan_create": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "amr_transfer_plan_interpolate": ([ctypes.c_void_p] * 4, ctypes.c_int),
@@ -52,6 +57,11 @@ ENTRY_POINTS = {
     "amr_transfer_plan_interpolate_adjoint": ([ctypes.c_void_p] * 4, ctypes.c_int),
     "amr_transfer_plan_restrict_adjoint": ([ctypes.c_void_p] * 4, ctypes.c_int),
     "amr_transfer_plan_get_info": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "amr_transfer_plan_get_tuning": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "amr_transfer_plan_set_tuning": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "amr_transfer_plan_autotune": ([ctypes.c_void_p] * 6, ctypes.c_int),
+    "amr_transfer_plan_capture_step": ([ctypes.c_void_p] * 4, ctypes.c_int),
+    "amr_transfer_plan_launch_step": ([ctypes.c_void_p] * 2, ctypes.c_int),
     "amr_transfer_plan_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "amr_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "amr_last_cuda_error": ([], ctypes.c_char_p),
@@ -158,6 +168,36 @@ class Plan:
             self._handle, self._sized(g_coarse, self.coarse_elems, "g_coarse"),
             self._sized(g_fine, self.fine_elems, "g_fine"), _stream(stream)), "restrict_adjoint")
         return g_fine
+
+    @property
+    def tuning(self):
+        out = Tuning()
+        _check(lib().amr_transfer_plan_get_tuning(self._handle, ctypes.byref(out)), "get_tuning")
+        return {name: getattr(out, name) for name, _ in Tuning._fields_ if name != "reserved"}
+
+    def set_tuning(self, interp_threads, interp_smem_budget, restrict_threads):
+        t = Tuning(int(interp_threads), int(interp_smem_budget), int(restrict_threads), 0)
+        _check(lib().amr_transfer_plan_set_tuning(self._handle, ctypes.byref(t)), "set_tuning")
+
+    def autotune(self, coarse, fine, coarse_out, stream=None):
+        """Time candidate launch shapes on these buffers and keep the fastest
+        (overwrites fine's ghost halves and coarse_out's restricted volumes)."""
+        out = Tuning()
+        _check(lib().amr_transfer_plan_autotune(self._handle, self._sized(coarse, self.coarse_elems, "coarse"),
+                                                self._sized(fine, self.fine_elems, "fine"),
+                                                self._sized(coarse_out, self.coarse_elems, "coarse_out"),
+                                                _stream(stream), ctypes.byref(out)), "autotune")
+        return {name: getattr(out, name) for name, _ in Tuning._fields_ if name != "reserved"}
+
+    def capture_step(self, coarse, fine, coarse_out):
+        """Capture interpolate(coarse -> fine) + restrict(fine -> coarse_out) as a CUDA graph."""
+        _check(lib().amr_transfer_plan_capture_step(self._handle, self._sized(coarse, self.coarse_elems, "coarse"),
+                                                    self._sized(fine, self.fine_elems, "fine"),
+                                                    self._sized(coarse_out, self.coarse_elems, "coarse_out")),
+               "capture_step")
+
+    def launch_step(self, stream=None):
+        _check(lib().amr_transfer_plan_launch_step(self._handle, _stream(stream)), "launch_step")
 
     @property
     def info(self):

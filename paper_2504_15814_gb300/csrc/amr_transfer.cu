@@ -28,8 +28,8 @@ amr_status cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
   } while (0)
 
-constexpr int kThreads = 256;
-constexpr int kSmemBudget = 64 * 1024;  // dynamic shared memory per interpolation CTA
+constexpr int kThreads = 256;           // default CTA size
+constexpr int kSmemBudget = 64 * 1024;  // default shared memory budget per interpolation tile
 
 std::mutex g_tables_mutex;
 std::vector<int> g_tables_ready;  // per device
@@ -72,6 +72,28 @@ bool ranges_overlap(const void* a, int64_t abytes, const void* b, int64_t bbytes
 
 }  // namespace
 
+// Mean device time of `reps` runs of f on stream s (after one warm-up run).
+template <typename F>
+static amr_status time_runs(cudaStream_t s, int reps, F f, float* ms) {
+  cudaEvent_t a, b;
+  AMR_CUDA(cudaEventCreate(&a));
+  AMR_CUDA(cudaEventCreate(&b));
+  amr_status st = f();
+  if (st == AMR_OK) {
+    cudaEventRecord(a, s);
+    for (int r = 0; r < reps && st == AMR_OK; ++r) st = f();
+    cudaEventRecord(b, s);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (e != cudaSuccess) st = cuda_fail(e, "autotune timing");
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    *ms = t / reps;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return st;
+}
+
 struct amr_transfer_plan {
   int device = 0;
   int U = 0;
@@ -83,6 +105,8 @@ struct amr_transfer_plan {
   int n_itiles = 0, n_rtiles = 0;
   int interp_smem = 0;  // bytes of dynamic shared memory per interpolation CTA
   amr_transfer_plan_info info{};
+  amr_transfer_tuning tuning{kThreads, kSmemBudget, kThreads, 0};
+  cudaGraphExec_t step_exec = nullptr;
   // adjoint tables, built on the first adjoint call
   std::vector<amr_transfer_item> items_h;
   bool adj_ready = false;
@@ -94,8 +118,14 @@ struct amr_transfer_plan {
   double *pt_val_d = nullptr, *rt_val_d = nullptr;
 };
 
+static void drop_graph(amr_transfer_plan* p) {
+  if (p->step_exec) cudaGraphExecDestroy(p->step_exec);
+  p->step_exec = nullptr;
+}
+
 static void free_plan(amr_transfer_plan* p) {
   if (!p) return;
+  drop_graph(p);
   void* ptrs[] = {p->items_d, p->itiles_d, p->rtiles_d, p->pt_tiles_d, p->rt_tiles_d, p->group_ptr_d,
                   p->group_items_d, p->item_class_d, p->cls_pt_rows_d, p->cls_rt_rows_d, p->pt_row_ptr_d,
                   p->rt_row_ptr_d, p->pt_col_d, p->rt_col_d, p->pt_val_d, p->rt_val_d};
@@ -151,13 +181,19 @@ const char* amr_status_string(amr_status s) {
 
 const char* amr_last_cuda_error(void) { return g_cuda_error.c_str(); }
 
-amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_plan** out) {
-  if (!out) return AMR_ERR_INVALID_ARGUMENT;
-  *out = nullptr;
-  if (!desc) return AMR_ERR_INVALID_ARGUMENT;
+// (Re)build the forward tiles of a plan for its tuning (synchronous).
+static amr_status rebuild_tiles(amr_transfer_plan* p) {
+  amr_transfer_desc d{};
+  d.abi_version = AMR_TRANSFER_ABI_VERSION;
+  d.num_unknowns = p->U;
+  d.precision = p->precision;
+  d.num_items = (int64_t)p->items_h.size();
+  d.items = p->items_h.data();
+  d.coarse_elems = p->coarse_elems;
+  d.fine_elems = p->fine_elems;
   amr::BuildResult br;
   try {
-    br = amr::build_plan(*desc, kSmemBudget);
+    br = amr::build_plan(d, p->tuning.interp_smem_budget);
   } catch (const std::bad_alloc&) {
     return AMR_ERR_OUT_OF_MEMORY;
   }
@@ -167,11 +203,60 @@ amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_
   }
   if (br.interp_tiles.size() > (size_t)INT32_MAX || br.restrict_tiles.size() > (size_t)INT32_MAX)
     return AMR_ERR_UNSUPPORTED;
+  if (br.max_interp_smem > 227 * 1024) return AMR_ERR_UNSUPPORTED;
+  amr::Tile *it = nullptr, *rt = nullptr;
+  amr_status st;
+  if ((st = upload(br.interp_tiles, &it)) != AMR_OK || (st = upload(br.restrict_tiles, &rt)) != AMR_OK) {
+    cudaFree(it);
+    return st;
+  }
+  if (br.max_interp_smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(amr::interp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         br.max_interp_smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(amr::interp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               br.max_interp_smem);
+    if (e != cudaSuccess) {
+      cudaFree(it);
+      cudaFree(rt);
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    }
+  }
+  cudaFree(p->itiles_d);
+  cudaFree(p->rtiles_d);
+  p->itiles_d = it;
+  p->rtiles_d = rt;
+  p->n_itiles = (int)br.interp_tiles.size();
+  p->n_rtiles = (int)br.restrict_tiles.size();
+  p->interp_smem = br.max_interp_smem;
+  p->info.num_items = d.num_items;
+  p->info.interp_outputs = br.interp_outputs;
+  p->info.restrict_outputs = br.restrict_outputs;
+  p->info.interp_bytes = br.interp_bytes;
+  p->info.restrict_bytes = br.restrict_bytes;
+  p->info.interp_launches = p->n_itiles > 0 ? 1 : 0;
+  p->info.restrict_launches = p->n_rtiles > 0 ? 1 : 0;
+  return AMR_OK;
+}
+
+amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_plan** out) {
+  if (!out) return AMR_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  if (!desc) return AMR_ERR_INVALID_ARGUMENT;
+  amr::BuildResult br;
+  try {
+    br = amr::build_plan(*desc, kSmemBudget);  // validation (tiles are rebuilt below)
+  } catch (const std::bad_alloc&) {
+    return AMR_ERR_OUT_OF_MEMORY;
+  }
+  if (br.status != AMR_OK) {
+    g_cuda_error = br.message;
+    return br.status;
+  }
   int device = 0;
   AMR_CUDA(cudaGetDevice(&device));
   amr_status st = upload_tables(device);
   if (st != AMR_OK) return st;
-
   amr_transfer_plan* p = new (std::nothrow) amr_transfer_plan;
   if (!p) return AMR_ERR_OUT_OF_MEMORY;
   p->device = device;
@@ -180,28 +265,10 @@ amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_
   p->coarse_elems = desc->coarse_elems;
   p->fine_elems = desc->fine_elems;
   p->items_h.assign(desc->items, desc->items + desc->num_items);
-  if ((st = upload(p->items_h, &p->items_d)) != AMR_OK ||
-      (st = upload(br.interp_tiles, &p->itiles_d)) != AMR_OK ||
-      (st = upload(br.restrict_tiles, &p->rtiles_d)) != AMR_OK) {
+  if ((st = upload(p->items_h, &p->items_d)) != AMR_OK || (st = rebuild_tiles(p)) != AMR_OK) {
     free_plan(p);
     return st;
   }
-  p->n_itiles = (int)br.interp_tiles.size();
-  p->n_rtiles = (int)br.restrict_tiles.size();
-  p->interp_smem = br.max_interp_smem;
-  if (p->interp_smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(amr::interp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(amr::interp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->interp_smem);
-    if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaFuncSetAttribute"); }
-  }
-  p->info.num_items = desc->num_items;
-  p->info.interp_outputs = br.interp_outputs;
-  p->info.restrict_outputs = br.restrict_outputs;
-  p->info.interp_bytes = br.interp_bytes;
-  p->info.restrict_bytes = br.restrict_bytes;
-  p->info.interp_launches = p->n_itiles > 0 ? 1 : 0;
-  p->info.restrict_launches = p->n_rtiles > 0 ? 1 : 0;
   *out = p;
   return AMR_OK;
 }
@@ -223,9 +290,11 @@ amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coa
   if (p->n_itiles == 0) return AMR_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (p->precision == AMR_PREC_SPLIT)
-    amr::interp_kernel<true><<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
+    amr::interp_kernel<true><<<p->n_itiles, p->tuning.interp_threads, p->interp_smem, s>>>(p->items_d, p->itiles_d,
+                                                                                          p->U, coarse, fine);
   else
-    amr::interp_kernel<false><<<p->n_itiles, kThreads, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine);
+    amr::interp_kernel<false><<<p->n_itiles, p->tuning.interp_threads, p->interp_smem, s>>>(p->items_d, p->itiles_d,
+                                                                                           p->U, coarse, fine);
   AMR_CUDA(cudaGetLastError());
   return AMR_OK;
 }
@@ -236,9 +305,11 @@ amr_status amr_transfer_plan_restrict(amr_transfer_plan* p, const double* fine, 
   if (p->n_rtiles == 0) return AMR_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (p->precision == AMR_PREC_SPLIT)
-    amr::restrict_kernel<true><<<p->n_rtiles, kThreads, 0, s>>>(p->items_d, p->rtiles_d, p->U, fine, coarse);
+    amr::restrict_kernel<true><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(p->items_d, p->rtiles_d, p->U,
+                                                                                  fine, coarse);
   else
-    amr::restrict_kernel<false><<<p->n_rtiles, kThreads, 0, s>>>(p->items_d, p->rtiles_d, p->U, fine, coarse);
+    amr::restrict_kernel<false><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(p->items_d, p->rtiles_d, p->U,
+                                                                                   fine, coarse);
   AMR_CUDA(cudaGetLastError());
   return AMR_OK;
 }
@@ -272,6 +343,109 @@ amr_status amr_transfer_plan_restrict_adjoint(amr_transfer_plan* p, const double
                                                                     g_coarse, g_fine);
     AMR_CUDA(cudaGetLastError());
   }
+  return AMR_OK;
+}
+
+amr_status amr_transfer_plan_get_tuning(const amr_transfer_plan* p, amr_transfer_tuning* out) {
+  if (!p || !out) return AMR_ERR_INVALID_ARGUMENT;
+  *out = p->tuning;
+  return AMR_OK;
+}
+
+static bool tuning_valid(const amr_transfer_tuning& t) {
+  auto ok_threads = [](int n) { return n >= 32 && n <= 256 && n % 32 == 0; };
+  return ok_threads(t.interp_threads) && ok_threads(t.restrict_threads) && t.interp_smem_budget >= 4096 &&
+         t.interp_smem_budget <= 196 * 1024 && t.reserved == 0;
+}
+
+amr_status amr_transfer_plan_set_tuning(amr_transfer_plan* p, const amr_transfer_tuning* t) {
+  if (!p || !t || !tuning_valid(*t)) return AMR_ERR_INVALID_ARGUMENT;
+  drop_graph(p);
+  const amr_transfer_tuning old = p->tuning;
+  p->tuning = *t;
+  amr_status st = rebuild_tiles(p);
+  if (st != AMR_OK) {
+    p->tuning = old;
+    rebuild_tiles(p);
+  }
+  return st;
+}
+
+amr_status amr_transfer_plan_autotune(amr_transfer_plan* p, const double* coarse, double* fine, double* coarse_out,
+                                      void* stream, amr_transfer_tuning* chosen) {
+  amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, fine, p ? p->fine_elems : 0);
+  if (st != AMR_OK) return st;
+  if ((st = check_call(p, fine, p->fine_elems, coarse_out, p->coarse_elems)) != AMR_OK) return st;
+  drop_graph(p);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int reps = 3;
+  amr_transfer_tuning best = p->tuning;
+  float best_i = 1e30f, best_r = 1e30f;
+  const int threads[] = {128, 256};
+  const int budgets[] = {24 * 1024, 32 * 1024, 48 * 1024, 64 * 1024, 96 * 1024};
+  for (int th : threads)
+    for (int bud : budgets) {
+      amr_transfer_tuning t = p->tuning;
+      t.interp_threads = th;
+      t.interp_smem_budget = bud;
+      p->tuning = t;
+      if ((st = rebuild_tiles(p)) != AMR_OK) continue;  // e.g. a budget the device cannot hold
+      float ms = 0.f;
+      if ((st = time_runs(s, reps, [&] { return amr_transfer_plan_interpolate(p, coarse, fine, stream); }, &ms)) !=
+          AMR_OK)
+        return st;
+      if (ms < best_i) {
+        best_i = ms;
+        best.interp_threads = th;
+        best.interp_smem_budget = bud;
+      }
+    }
+  for (int th : threads) {
+    p->tuning.restrict_threads = th;
+    float ms = 0.f;
+    if ((st = time_runs(s, reps, [&] { return amr_transfer_plan_restrict(p, fine, coarse_out, stream); }, &ms)) !=
+        AMR_OK)
+      return st;
+    if (ms < best_r) {
+      best_r = ms;
+      best.restrict_threads = th;
+    }
+  }
+  p->tuning = best;
+  if ((st = rebuild_tiles(p)) != AMR_OK) return st;
+  if (chosen) *chosen = best;
+  return AMR_OK;
+}
+
+amr_status amr_transfer_plan_capture_step(amr_transfer_plan* p, const double* coarse, double* fine,
+                                          double* coarse_out) {
+  amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, fine, p ? p->fine_elems : 0);
+  if (st != AMR_OK) return st;
+  if ((st = check_call(p, fine, p->fine_elems, coarse_out, p->coarse_elems)) != AMR_OK) return st;
+  drop_graph(p);
+  cudaStream_t cs;
+  AMR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    st = amr_transfer_plan_interpolate(p, coarse, fine, cs);
+    if (st == AMR_OK) st = amr_transfer_plan_restrict(p, fine, coarse_out, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+  }
+  if (e == cudaSuccess && st == AMR_OK) e = cudaGraphInstantiate(&p->step_exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (st != AMR_OK) return st;
+  if (e != cudaSuccess) {
+    p->step_exec = nullptr;
+    return cuda_fail(e, "step graph capture");
+  }
+  return AMR_OK;
+}
+
+amr_status amr_transfer_plan_launch_step(amr_transfer_plan* p, void* stream) {
+  if (!p || !p->step_exec) return AMR_ERR_INVALID_ARGUMENT;
+  AMR_CUDA(cudaGraphLaunch(p->step_exec, (cudaStream_t)stream));
   return AMR_OK;
 }
 
