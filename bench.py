@@ -210,8 +210,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = B.PREC_SPLIT if args.precision == "split" else B.PREC_FP64
-    items, coarse, fine = wl.uniform_batch(n_faces=args.faces, p=P, k=K, U=U, order=3, config_index=1,
-                                           device=dev)
+    # weak scaling: a global batch of faces-per-GPU x N faces, each rank
+    # keeping its cost-balanced shard (items are independent: no collective)
+    items, coarse, fine = wl.uniform_batch(n_faces=args.faces * world, p=P, k=K, U=U, order=3, config_index=1,
+                                           device=dev, shard=(rank, world) if world > 1 else None)
     coarse_out = coarse.clone()
     plan = B.Plan(items, U, coarse.numel(), fine.numel(), prec)
     info = plan.info
@@ -247,7 +249,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     outs = (info["interp_outputs"] + info["restrict_outputs"]) * U
-    value = outs * world / (ms * 1e-3)
+    total_outs = outs
+    if dist:
+        t = torch.tensor([float(outs)], device=dev, dtype=torch.float64)
+        dist.all_reduce(t)
+        total_outs = float(t.item())
+    value = total_outs / (ms * 1e-3)
 
     peaks, peak_src = measured_peaks()
     hbm_peak = float(peaks["hbm_gbs"])

@@ -185,9 +185,11 @@ def origins_in_box(n, rng, box=64.0):
 
 
 def uniform_batch(n_faces=2048, p=9, k=3, U=59, order=3, config_index=1, device="cpu",
-                  noise=1e-8, faces=None):
+                  noise=1e-8, faces=None, shard=None):
     """Hanging faces as whole-face items (nine subfaces each), faces cycled
-    0..5, smooth fields.  Returns (items, coarse, fine)."""
+    0..5, smooth fields.  shard=(rank, world) keeps only that rank's
+    cost-balanced share of the n_faces items, on compact local buffers.
+    Returns (items, coarse, fine)."""
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + config_index))
     if faces is None:
         faces = [i % 6 for i in range(n_faces)]
@@ -195,6 +197,12 @@ def uniform_batch(n_faces=2048, p=9, k=3, U=59, order=3, config_index=1, device=
                                [order] * n_faces, U)
     origins = origins_in_box(n_faces, rng)
     field = SmoothField(U, rng, device=device)
+    if shard is not None:
+        from .sharding import local_items, shard_bounds
+        rank, world = shard
+        lo, hi = shard_bounds(items, world)[rank]
+        items, cl, fl, _, _ = local_items(items, U, lo, hi)
+        origins = origins[lo:hi]
     coarse, fine = sample_buffers(items, U, cl, fl, field, origins, device)
     add_noise(coarse, noise, rng)
     add_noise(fine, noise, rng)
