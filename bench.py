@@ -216,8 +216,9 @@ def main():
                                            device=dev, shard=(rank, world) if world > 1 else None)
     coarse_out = coarse.clone()
     plan = B.Plan(items, U, coarse.numel(), fine.numel(), prec)
-    info = plan.info
     stream = torch.cuda.current_stream(dev)
+    tuning = plan.autotune(coarse, fine, coarse_out)  # launch shapes for this GPU, before timing
+    info = plan.info
 
     def step():
         plan.interpolate(coarse, fine)
@@ -275,6 +276,7 @@ def main():
                                    f"FP64 AoS, Taylor-3 interpolate+restrict",
                        "faces_per_gpu": args.faces, "p": P, "k": K, "U": U, "order": 3,
                        "precision": args.precision, "parallelism": f"dp{world}" if world > 1 else "single GPU",
+                       "tuning": tuning,
                        "l2": "inputs (4.7 GB) larger than L2, no flush"},
             "roofline": roofline, "clocks": clocks,
             "gpu_launches": args.steps * (info["interp_launches"] + info["restrict_launches"])}
@@ -426,6 +428,7 @@ def compare_paths(B, wl, items, coarse, fine, coarse_out, U, args, stream, plan_
             it = items.copy()
             it["order"] = order
             plan = B.Plan(it, U, coarse.numel(), fine.numel(), prec)
+            plan.autotune(coarse, fine, coarse_out)
             info = plan.info
             step = lambda: (plan.interpolate(coarse, fine), plan.restrict(fine, coarse_out))
             for _ in range(3):

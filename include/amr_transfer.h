@@ -149,12 +149,15 @@ amr_status amr_transfer_plan_get_info(const amr_transfer_plan* plan, amr_transfe
 /* Launch shapes of a plan.  interp_threads / restrict_threads: CTA size of
  * the two kernels (32..256, a multiple of 32); interp_smem_budget: bytes of
  * shared memory an interpolation tile may stage (4096..200704; it sets how
- * many unknowns one tile carries). */
+ * many unknowns one tile carries); interp_addback (split precision only,
+ * 0..3): share of the interpolated children whose float64 result is formed
+ * by one float64 add instead of float32 TwoSum + integer assembly -- 0 none,
+ * 1 four ninths, 2 two thirds (default), 3 eight ninths. */
 typedef struct {
   int32_t interp_threads;
   int32_t interp_smem_budget;
   int32_t restrict_threads;
-  int32_t reserved; /* 0 */
+  int32_t interp_addback;
 } amr_transfer_tuning;
 
 amr_status amr_transfer_plan_get_tuning(const amr_transfer_plan* plan, amr_transfer_tuning* out);

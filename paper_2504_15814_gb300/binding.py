@@ -47,7 +47,7 @@ class PlanInfo(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("interp_threads", ctypes.c_int32), ("interp_smem_budget", ctypes.c_int32),
-                ("restrict_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("restrict_threads", ctypes.c_int32), ("interp_addback", ctypes.c_int32)]
 
 
 ENTRY_POINTS = {
@@ -173,10 +173,10 @@ class Plan:
     def tuning(self):
         out = Tuning()
         _check(lib().amr_transfer_plan_get_tuning(self._handle, ctypes.byref(out)), "get_tuning")
-        return {name: getattr(out, name) for name, _ in Tuning._fields_ if name != "reserved"}
+        return {name: getattr(out, name) for name, _ in Tuning._fields_}
 
-    def set_tuning(self, interp_threads, interp_smem_budget, restrict_threads):
-        t = Tuning(int(interp_threads), int(interp_smem_budget), int(restrict_threads), 0)
+    def set_tuning(self, interp_threads, interp_smem_budget, restrict_threads, interp_addback=2):
+        t = Tuning(int(interp_threads), int(interp_smem_budget), int(restrict_threads), int(interp_addback))
         _check(lib().amr_transfer_plan_set_tuning(self._handle, ctypes.byref(t)), "set_tuning")
 
     def autotune(self, coarse, fine, coarse_out, stream=None):
@@ -187,7 +187,7 @@ class Plan:
                                                 self._sized(fine, self.fine_elems, "fine"),
                                                 self._sized(coarse_out, self.coarse_elems, "coarse_out"),
                                                 _stream(stream), ctypes.byref(out)), "autotune")
-        return {name: getattr(out, name) for name, _ in Tuning._fields_ if name != "reserved"}
+        return {name: getattr(out, name) for name, _ in Tuning._fields_}
 
     def capture_step(self, coarse, fine, coarse_out):
         """Capture interpolate(coarse -> fine) + restrict(fine -> coarse_out) as a CUDA graph."""

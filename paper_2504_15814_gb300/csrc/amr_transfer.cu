@@ -105,7 +105,7 @@ struct amr_transfer_plan {
   int n_itiles = 0, n_rtiles = 0;
   int interp_smem = 0;  // bytes of dynamic shared memory per interpolation CTA
   amr_transfer_plan_info info{};
-  amr_transfer_tuning tuning{kThreads, kSmemBudget, kThreads, 0};
+  amr_transfer_tuning tuning{kThreads, kSmemBudget, kThreads, 2};
   cudaGraphExec_t step_exec = nullptr;
   // adjoint tables, built on the first adjoint call
   std::vector<amr_transfer_item> items_h;
@@ -211,11 +211,12 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
     return st;
   }
   if (br.max_interp_smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(amr::interp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         br.max_interp_smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(amr::interp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               br.max_interp_smem);
+    const void* fns[5] = {(const void*)amr::interp_kernel<false>, (const void*)amr::interp_kernel<true, 0>,
+                          (const void*)amr::interp_kernel<true, 1>, (const void*)amr::interp_kernel<true, 2>,
+                          (const void*)amr::interp_kernel<true, 3>};
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 5 && e == cudaSuccess; ++q)
+      e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, br.max_interp_smem);
     if (e != cudaSuccess) {
       cudaFree(it);
       cudaFree(rt);
@@ -289,10 +290,15 @@ amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coa
   if (st != AMR_OK) return st;
   if (p->n_itiles == 0) return AMR_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (p->precision == AMR_PREC_SPLIT)
-    amr::interp_kernel<true><<<p->n_itiles, p->tuning.interp_threads, p->interp_smem, s>>>(p->items_d, p->itiles_d,
-                                                                                          p->U, coarse, fine);
-  else
+  if (p->precision == AMR_PREC_SPLIT) {
+    const dim3 g(p->n_itiles), b(p->tuning.interp_threads);
+    switch (p->tuning.interp_addback) {
+      case 0: amr::interp_kernel<true, 0><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine); break;
+      case 1: amr::interp_kernel<true, 1><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine); break;
+      case 3: amr::interp_kernel<true, 3><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine); break;
+      default: amr::interp_kernel<true, 2><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine); break;
+    }
+  } else
     amr::interp_kernel<false><<<p->n_itiles, p->tuning.interp_threads, p->interp_smem, s>>>(p->items_d, p->itiles_d,
                                                                                            p->U, coarse, fine);
   AMR_CUDA(cudaGetLastError());
@@ -355,7 +361,7 @@ amr_status amr_transfer_plan_get_tuning(const amr_transfer_plan* p, amr_transfer
 static bool tuning_valid(const amr_transfer_tuning& t) {
   auto ok_threads = [](int n) { return n >= 32 && n <= 256 && n % 32 == 0; };
   return ok_threads(t.interp_threads) && ok_threads(t.restrict_threads) && t.interp_smem_budget >= 4096 &&
-         t.interp_smem_budget <= 196 * 1024 && t.reserved == 0;
+         t.interp_smem_budget <= 196 * 1024 && t.interp_addback >= 0 && t.interp_addback <= 3;
 }
 
 amr_status amr_transfer_plan_set_tuning(amr_transfer_plan* p, const amr_transfer_tuning* t) {
@@ -400,6 +406,22 @@ amr_status amr_transfer_plan_autotune(amr_transfer_plan* p, const double* coarse
         best.interp_smem_budget = bud;
       }
     }
+  if (p->precision == AMR_PREC_SPLIT) {
+    p->tuning = best;
+    if ((st = rebuild_tiles(p)) != AMR_OK) return st;
+    for (int mode = 0; mode <= 3; ++mode) {
+      p->tuning.interp_addback = mode;
+      float ms = 0.f;
+      if ((st = time_runs(s, reps, [&] { return amr_transfer_plan_interpolate(p, coarse, fine, stream); }, &ms)) !=
+          AMR_OK)
+        return st;
+      if (ms < best_i) {
+        best_i = ms;
+        best.interp_addback = mode;
+      }
+    }
+    p->tuning = best;
+  }
   for (int th : threads) {
     p->tuning.restrict_threads = th;
     float ms = 0.f;

@@ -275,10 +275,11 @@ __device__ __forceinline__ ChildMap child_map(const Tile& t, int p, int a, int b
     s0 = t.sub % 3;
     s1 = t.sub / 3;
     m.slot = t.slot;
-  } else {  // whole-face tile: the subface follows from the centre
-    const int w = p / 3;
-    s0 = a / w;
-    s1 = b / w;
+  } else {  // whole-face tile: the subface follows from the centre;
+            // (a + 1/2) / w is never within 1/32 of an integer (w <= 16)
+    const float inv_w = 3.0f / (float)p;
+    s0 = (int)(((float)a + 0.5f) * inv_w);
+    s1 = (int)(((float)b + 0.5f) * inv_w);
     m.slot = s0 + 3 * s1;
   }
   m.q0_off = 1 - s0 * p;
@@ -311,13 +312,15 @@ struct Counter4 {
 // Split mode: the stencil differences come from the pairs and the derivative
 // and Taylor arithmetic is float32; the child coincident with the centre is
 // the centre's own float64 value; the other children are rebuilt as float64
-// from base + increment, two thirds of them (tangential offset e1 <= 0) by one
-// float64 add of the exactly converted increment, the rest by TwoSum +
-// integer assembly without any float64 instruction -- this balances the
-// GB300 float64 unit (about 1/73 of the float32 rate) against the
-// integer/float32 issue slots.
+// from base + increment, either by one float64 add of the exactly converted
+// increment or by TwoSum + integer assembly without any float64 instruction.
+// The share of each (ADDBACK) balances the GB300 float64 unit (about 1/73 of
+// the float32 rate) against the integer issue slots; the autotuner picks it.
 // ---------------------------------------------------------------------------
-template <bool SPLIT>
+// ADDBACK (split mode): which children add the increment with one float64
+// add (the rest use the integer assembly): 0 none, 1 e0 <= 0 and e1 <= 0
+// (4/9), 2 e1 <= 0 (2/3), 3 all but e0 = e1 = +1 (8/9).
+template <bool SPLIT, int ADDBACK = 2>
 __global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_transfer_item* __restrict__ items,
                                                      const Tile* __restrict__ tiles, int U,
                                                      const double* __restrict__ coarse,
@@ -385,7 +388,9 @@ __global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_tr
       auto emit = [&](int ii, int e0, int e1, float incr) {
         double v;
         if (ii == 1 && e0 == 0 && e1 == 0) v = base;
-        else if (e1 <= 0) v = __dadd_rn(base, f32_to_f64(incr));
+        else if ((ADDBACK == 1 && e0 <= 0 && e1 <= 0) || (ADDBACK == 2 && e1 <= 0) ||
+                 (ADDBACK == 3 && (e0 < 1 || e1 < 1)))
+          v = __dadd_rn(base, f32_to_f64(incr));
         else v = add_back(hc, incr);
         store(ii, e0, e1, v);
       };
@@ -408,10 +413,6 @@ __global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_tr
 // layer j.
 // ---------------------------------------------------------------------------
 
-// Extrapolated coarse halo layer j of a Taylor restriction in split mode,
-// from the loaded window values v[0..L) (expansion value v[pos]): exact
-// float-pair differences, float-pair weighted sum, float64 rebuilt without
-// float64 instructions.
 __device__ __forceinline__ double pick5(const double* v, int idx) {
   double r = v[0];
 #pragma unroll
@@ -419,32 +420,46 @@ __device__ __forceinline__ double pick5(const double* v, int idx) {
   return r;
 }
 
-__device__ __forceinline__ double taylor_extrapolate_split(const double* v, int L, int pos, int m, int k, int j) {
+// Taylor restriction in split mode, window values v[0..L) already loaded
+// (expansion value v[pos]): exact float-pair differences to the expansion
+// value, formed once per column; per extrapolated layer j a float-pair
+// weighted sum; each output rebuilt as float64 without float64 instructions.
+template <typename Store>
+__device__ __forceinline__ void taylor_extrapolate_split(const double* v, int L, int pos, int m, int k,
+                                                         const Store& store) {
   const F2 b = split_f64(pick5(v, pos));
-  const int w0 = rw_index(m, k, j);
-  float ah = 0.f, al = 0.f;
+  float dh[5], dl[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
+    dh[i] = 0.f;
+    dl[i] = 0.f;
     if (i < L && i != pos) {
       const F2 x = split_f64(v[i]);
       float e;
-      const float dh = two_sum(x.hi, -b.hi, e);
-      const float dl = __fadd_rn(e, __fsub_rn(x.lo, b.lo));
+      dh[i] = two_sum(x.hi, -b.hi, e);
+      dl[i] = __fadd_rn(e, __fsub_rn(x.lo, b.lo));
+    }
+  }
+  for (int j = 1; j < k; ++j) {
+    const int w0 = rw_index(m, k, j);
+    float ah = 0.f, al = 0.f;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
       const float wh = c_rw_hi[w0 + i], wl = c_rw_lo[w0 + i];
-      const float pr = __fmul_rn(wh, dh);
-      float pe = __fmaf_rn(wh, dh, -pr);  // exact product error
-      pe = __fmaf_rn(wh, dl, pe);
-      pe = __fmaf_rn(wl, dh, pe);
+      const float pr = __fmul_rn(wh, dh[i]);
+      float pe = __fmaf_rn(wh, dh[i], -pr);  // exact product error
+      pe = __fmaf_rn(wh, dl[i], pe);
+      pe = __fmaf_rn(wl, dh[i], pe);
       float t;
       ah = two_sum(ah, pr, t);
       al = __fadd_rn(al, __fadd_rn(t, pe));
     }
+    float e1, e2;
+    const float s1 = two_sum(b.hi, ah, e1);
+    const float tt = __fadd_rn(__fadd_rn(e1, b.lo), al);
+    const float s2 = fast_two_sum(s1, tt, e2);
+    store(j, pair_to_f64(s2, e2));
   }
-  float e1, e2;
-  const float s1 = two_sum(b.hi, ah, e1);
-  const float tt = __fadd_rn(__fadd_rn(e1, b.lo), al);
-  const float s2 = fast_two_sum(s1, tt, e2);
-  return pair_to_f64(s2, e2);
 }
 
 // d-linear, float64: tangential 3x3 average per fine layer, least-squares
@@ -561,19 +576,18 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (!ccol[r]) continue;
-        ccol[r][0] = pick5(v[r], 1 - s);  // layer 0 coincides with fine layer 1
-        for (int j = 1; j < k; ++j) {
-          double out;
-          if (SPLIT) {
-            out = taylor_extrapolate_split(v[r], L, pos, m, k, j);
-          } else {
+        double* col = ccol[r];
+        col[0] = pick5(v[r], 1 - s);  // layer 0 coincides with fine layer 1
+        if (SPLIT) {
+          taylor_extrapolate_split(v[r], L, pos, m, k, [&](int j, double out) { col[j * gs_n] = out; });
+        } else {
+          for (int j = 1; j < k; ++j) {
             const double* w = c_rw + rw_index(m, k, j);
             double acc = 0.0;
 #pragma unroll
             for (int i = 0; i < 5; ++i) acc = fma(w[i], v[r][i], acc);
-            out = acc;
+            col[j * gs_n] = acc;
           }
-          ccol[r][j * gs_n] = out;
         }
       }
     }

@@ -37,25 +37,28 @@ def _check(items, U, c, f, f_gpu, c_gpu, tol):
     assert normwise_errors(items, U, c_gpu, c_ref, cm, "coarse")[0] <= tol
 
 
-@pytest.mark.parametrize("shape", [(128, 8192, 128), (256, 24 * 1024, 64), (64, 100 * 1024, 256)])
-def test_set_tuning_keeps_parity(shape):
+@pytest.mark.parametrize("precision,tol", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6)])
+@pytest.mark.parametrize("shape", [(128, 8192, 128, 0), (256, 24 * 1024, 64, 1), (64, 100 * 1024, 256, 3),
+                                   (256, 64 * 1024, 256, 2)])
+def test_set_tuning_keeps_parity(shape, precision, tol):
     U = 13
     items, c, f = _batch(U=U)
-    plan = B.Plan(items, U, len(c), len(f), B.PREC_FP64)
+    plan = B.Plan(items, U, len(c), len(f), precision)
     plan.set_tuning(*shape)
-    assert plan.tuning == dict(interp_threads=shape[0], interp_smem_budget=shape[1], restrict_threads=shape[2])
+    assert plan.tuning == dict(interp_threads=shape[0], interp_smem_budget=shape[1], restrict_threads=shape[2],
+                               interp_addback=shape[3])
     cd, fd = torch.as_tensor(c).cuda(), torch.as_tensor(f).cuda()
     co = cd.clone()
     plan.interpolate(cd, fd)
     plan.restrict(fd, co)
     torch.cuda.synchronize()
-    _check(items, U, c, f, fd.cpu().numpy(), co.cpu().numpy(), 1e-12)
+    _check(items, U, c, f, fd.cpu().numpy(), co.cpu().numpy(), tol)
 
 
 def test_invalid_tuning_rejected():
     items, c, f = _batch(n=2)
     plan = B.Plan(items, 13, len(c), len(f))
-    for bad in [(16, 32768, 128), (256, 1024, 128), (256, 32768, 300), (512, 32768, 128)]:
+    for bad in [(16, 32768, 128), (256, 1024, 128), (256, 32768, 300), (512, 32768, 128), (256, 32768, 128, 4)]:
         with pytest.raises(B.AmrError):
             plan.set_tuning(*bad)
 
