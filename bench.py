@@ -34,7 +34,7 @@ UNIT = "volume-unknowns/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["split", "fp64"], default="split")
@@ -103,6 +103,40 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    """sha256 of the CUDA/C++ sources of the library (sorted by name)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2504_15814_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".cpp", ".hpp")):
+            with open(os.path.join(d, name), "rb") as fh:
+                h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel, faces):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, scaled
+    to `faces` hanging faces, when the summary was taken on these exact
+    sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_uniform_batch_split.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    fields = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ": " in line:
+            key, val = line[2:].split(": ", 1)
+            fields[key.strip()] = val.strip().strip("`")
+    if fields.get("source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return float(fields["dram_bytes_per_face"]) * faces
+    except (KeyError, ValueError):
+        return None
 
 
 def measured_peaks():
@@ -262,11 +296,14 @@ def main():
     interp_gbs = info["interp_bytes"] / (t_interp * 1e-3) / 1e9
     restrict_gbs = info["restrict_bytes"] / (t_restrict * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": "interp_kernel", "achieved": interp_gbs, "peak": hbm_peak,
-                "unit": "GB/s", "frac": interp_gbs / hbm_peak, "traffic": None,
+                "unit": "GB/s", "frac": interp_gbs / hbm_peak,
+                "traffic": profiled_traffic("interp_kernel", args.faces) if prec == B.PREC_SPLIT else None,
                 "algorithmic_bytes_per_launch": info["interp_bytes"], "launch_ms": t_interp,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "restrict_kernel": {"achieved": restrict_gbs, "frac": restrict_gbs / hbm_peak,
-                                    "launch_ms": t_restrict, "algorithmic_bytes_per_launch": info["restrict_bytes"]}}
+                                    "launch_ms": t_restrict, "algorithmic_bytes_per_launch": info["restrict_bytes"],
+                                    "traffic": profiled_traffic("restrict_kernel", args.faces)
+                                    if prec == B.PREC_SPLIT else None}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -422,10 +422,10 @@ __device__ __forceinline__ double pick5(const double* v, int idx) {
 
 // Taylor restriction in split mode, window values v[0..L) already loaded
 // (expansion value v[pos]): exact float-pair differences to the expansion
-// value, formed once per column; per extrapolated layer j a float-pair
+// value, formed once per column; per extrapolated layer j >= j0 a float-pair
 // weighted sum; each output rebuilt as float64 without float64 instructions.
 template <typename Store>
-__device__ __forceinline__ void taylor_extrapolate_split(const double* v, int L, int pos, int m, int k,
+__device__ __forceinline__ void taylor_extrapolate_split(const double* v, int L, int pos, int m, int k, int j0,
                                                          const Store& store) {
   const F2 b = split_f64(pick5(v, pos));
   float dh[5], dl[5];
@@ -440,7 +440,7 @@ __device__ __forceinline__ void taylor_extrapolate_split(const double* v, int L,
       dl[i] = __fadd_rn(e, __fsub_rn(x.lo, b.lo));
     }
   }
-  for (int j = 1; j < k; ++j) {
+  for (int j = j0; j < k; ++j) {
     const int w0 = rw_index(m, k, j);
     float ah = 0.f, al = 0.f;
 #pragma unroll
@@ -579,7 +579,15 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
         double* col = ccol[r];
         col[0] = pick5(v[r], 1 - s);  // layer 0 coincides with fine layer 1
         if (SPLIT) {
-          taylor_extrapolate_split(v[r], L, pos, m, k, [&](int j, double out) { col[j * gs_n] = out; });
+          // layer 1 with float64 combined weights (the float64 unit is idle
+          // here), deeper layers with float-pair arithmetic: the two pipes
+          // share the work
+          const double* w = c_rw + rw_index(m, k, 1);
+          double acc = 0.0;
+#pragma unroll
+          for (int i = 0; i < 5; ++i) acc = fma(w[i], v[r][i], acc);
+          col[gs_n] = acc;
+          if (k > 2) taylor_extrapolate_split(v[r], L, pos, m, k, 2, [&](int j, double out) { col[j * gs_n] = out; });
         } else {
           for (int j = 1; j < k; ++j) {
             const double* w = c_rw + rw_index(m, k, j);
