@@ -385,6 +385,24 @@ def other_workloads(B, wl, stream):
                           "volume_unknowns_per_step": outs, "max_rel_err_vs_exact_quadratic": err,
                           "launches_per_step": 2}
     plan.close()
+    # float32 storage of the increments on the uniform batch (2,048 faces)
+    items, coarse, fine = wl.uniform_batch(n_faces=2048, U=59, order=3, config_index=1, device="cuda")
+    plan = B.Plan(items, 59, coarse.numel(), fine.numel(), B.PREC_SPLIT)
+    plan.autotune(coarse, fine, coarse.clone())
+    info = plan.info
+    incr = torch.empty(info["increment_elems"], dtype=torch.float32, device="cuda")
+    t_incr = _time_steps(lambda: plan.interpolate_increments(coarse, incr), 20, stream)
+    t_apply = _time_steps(lambda: plan.apply_increments(coarse, incr, fine), 20, stream)
+    read_b = info["interp_bytes"] - info["interp_outputs"] * 59 * 8
+    incr_b = read_b + info["increment_elems"] * 4
+    out["split_f32_increments"] = {
+        "workload": "2,048 hanging faces, p=9, k=3, U=59, Taylor-3: float32 increments instead of float64 ghosts",
+        "interpolate_increments_ms": t_incr, "algorithmic_bytes": incr_b,
+        "achieved_gbs": incr_b / (t_incr * 1e-3) / 1e9, "apply_increments_ms": t_apply,
+        "value": info["increment_elems"] / (t_incr * 1e-3), "unit": "interpolated volume-unknowns/s"}
+    plan.close()
+    del items, coarse, fine, incr
+    torch.cuda.empty_cache()
     # uneven batch: 20,000 subface items, p in {6,9,12}, k in {2,3}, orders 1/2/3
     items, coarse, fine = wl.uneven_batch(device="cuda")
     U = 59

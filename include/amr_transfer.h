@@ -132,6 +132,26 @@ amr_status amr_transfer_plan_interpolate_adjoint(amr_transfer_plan* plan, const 
 amr_status amr_transfer_plan_restrict_adjoint(amr_transfer_plan* plan, const double* g_coarse,
                                               double* g_fine, void* cuda_stream);
 
+/* Split precision with float32 storage of the increments.  For every fine
+ * ghost volume and unknown, writes increment = (interpolated value) - (value
+ * of the coarse centre nearest to it) as float32, computed exactly as in
+ * AMR_PREC_SPLIT (float64-accurate differences, float32 derivative and
+ * Taylor arithmetic); coincident volumes get 0.  Layout: item i's increments
+ * start at the sum over earlier items of (number of fine face arrays) * k *
+ * p^2 * U; inside an item, element (((s * k + g) * p + q1) * p + q0) * U + u
+ * for fine face array s, ghost layer g (0 next to the interface), tangential
+ * indices q1 (t1) and q0 (t0), unknown u.  increments holds
+ * amr_transfer_plan_info.increment_elems floats; d-linear items are included
+ * the same way.  Works for plans of either precision. */
+amr_status amr_transfer_plan_interpolate_increments(amr_transfer_plan* plan, const double* coarse,
+                                                    float* increments, void* cuda_stream);
+
+/* fine ghost value = coarse centre value + increment (float64 result), for
+ * the increments written by amr_transfer_plan_interpolate_increments from the
+ * same coarse buffer: writes the same fine entries as interpolate. */
+amr_status amr_transfer_plan_apply_increments(amr_transfer_plan* plan, const double* coarse,
+                                              const float* increments, double* fine, void* cuda_stream);
+
 /* Plan facts used to report throughput. */
 typedef struct {
   int64_t num_items;
@@ -142,6 +162,7 @@ typedef struct {
   int64_t restrict_bytes;      /* the same for one restrict */
   int32_t interp_launches;     /* kernels one interpolate call enqueues */
   int32_t restrict_launches;   /* kernels one restrict call enqueues */
+  int64_t increment_elems;     /* float32 values of the increment array (see _interpolate_increments) */
 } amr_transfer_plan_info;
 
 amr_status amr_transfer_plan_get_info(const amr_transfer_plan* plan, amr_transfer_plan_info* info);

@@ -42,7 +42,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("num_items", ctypes.c_int64), ("interp_outputs", ctypes.c_int64),
                 ("restrict_outputs", ctypes.c_int64), ("interp_bytes", ctypes.c_int64),
                 ("restrict_bytes", ctypes.c_int64), ("interp_launches", ctypes.c_int32),
-                ("restrict_launches", ctypes.c_int32)]
+                ("restrict_launches", ctypes.c_int32), ("increment_elems", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):
@@ -57,6 +57,8 @@ ENTRY_POINTS = {
     "amr_transfer_plan_interpolate_adjoint": ([ctypes.c_void_p] * 4, ctypes.c_int),
     "amr_transfer_plan_restrict_adjoint": ([ctypes.c_void_p] * 4, ctypes.c_int),
     "amr_transfer_plan_get_info": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "amr_transfer_plan_interpolate_increments": ([ctypes.c_void_p] * 4, ctypes.c_int),
+    "amr_transfer_plan_apply_increments": ([ctypes.c_void_p] * 5, ctypes.c_int),
     "amr_transfer_plan_get_tuning": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "amr_transfer_plan_set_tuning": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "amr_transfer_plan_autotune": ([ctypes.c_void_p] * 6, ctypes.c_int),
@@ -156,6 +158,32 @@ class Plan:
                                                 self._sized(coarse, self.coarse_elems, "coarse"), _stream(stream)),
                "restrict")
         return coarse
+
+    def _fptr(self, x, n, name):
+        """Device pointer of a contiguous float32 CUDA tensor holding >= n values."""
+        if isinstance(x, int):
+            return x
+        import torch
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+        if x.numel() < n:
+            raise ValueError(f"{name} holds {x.numel()} elements, the plan needs {n}")
+        return x.data_ptr()
+
+    def interpolate_increments(self, coarse, increments, stream=None):
+        """float32 increments (fine ghost value - nearest coarse centre value)."""
+        _check(lib().amr_transfer_plan_interpolate_increments(
+            self._handle, self._sized(coarse, self.coarse_elems, "coarse"),
+            self._fptr(increments, self.info["increment_elems"], "increments"), _stream(stream)),
+            "interpolate_increments")
+        return increments
+
+    def apply_increments(self, coarse, increments, fine, stream=None):
+        _check(lib().amr_transfer_plan_apply_increments(
+            self._handle, self._sized(coarse, self.coarse_elems, "coarse"),
+            self._fptr(increments, self.info["increment_elems"], "increments"),
+            self._sized(fine, self.fine_elems, "fine"), _stream(stream)), "apply_increments")
+        return fine
 
     def interpolate_adjoint(self, g_fine, g_coarse, stream=None):
         _check(lib().amr_transfer_plan_interpolate_adjoint(

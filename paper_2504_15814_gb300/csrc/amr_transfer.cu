@@ -103,6 +103,9 @@ struct amr_transfer_plan {
   amr::Tile* itiles_d = nullptr;
   amr::Tile* rtiles_d = nullptr;
   int n_itiles = 0, n_rtiles = 0;
+  int64_t* incr_off_d = nullptr;            // float32 increment offsets per item
+  amr::AdjointTile* incr_tiles_d = nullptr;  // apply_increments work
+  int n_incr_tiles = 0;
   int interp_smem = 0;  // bytes of dynamic shared memory per interpolation CTA
   amr_transfer_plan_info info{};
   amr_transfer_tuning tuning{kThreads, kSmemBudget, kThreads, 2};
@@ -126,7 +129,7 @@ static void drop_graph(amr_transfer_plan* p) {
 static void free_plan(amr_transfer_plan* p) {
   if (!p) return;
   drop_graph(p);
-  void* ptrs[] = {p->items_d, p->itiles_d, p->rtiles_d, p->pt_tiles_d, p->rt_tiles_d, p->group_ptr_d,
+  void* ptrs[] = {p->items_d, p->itiles_d, p->rtiles_d, p->incr_off_d, p->incr_tiles_d, p->pt_tiles_d, p->rt_tiles_d, p->group_ptr_d,
                   p->group_items_d, p->item_class_d, p->cls_pt_rows_d, p->cls_rt_rows_d, p->pt_row_ptr_d,
                   p->rt_row_ptr_d, p->pt_col_d, p->rt_col_d, p->pt_val_d, p->rt_val_d};
   for (void* q : ptrs) cudaFree(q);
@@ -205,28 +208,41 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
     return AMR_ERR_UNSUPPORTED;
   if (br.max_interp_smem > 227 * 1024) return AMR_ERR_UNSUPPORTED;
   amr::Tile *it = nullptr, *rt = nullptr;
+  int64_t* io = nullptr;
+  amr::AdjointTile* itl = nullptr;
   amr_status st;
-  if ((st = upload(br.interp_tiles, &it)) != AMR_OK || (st = upload(br.restrict_tiles, &rt)) != AMR_OK) {
+  if ((st = upload(br.interp_tiles, &it)) != AMR_OK || (st = upload(br.restrict_tiles, &rt)) != AMR_OK ||
+      (st = upload(br.incr_off, &io)) != AMR_OK || (st = upload(br.incr_tiles, &itl)) != AMR_OK) {
     cudaFree(it);
+    cudaFree(rt);
+    cudaFree(io);
     return st;
   }
   if (br.max_interp_smem > 48 * 1024) {
-    const void* fns[5] = {(const void*)amr::interp_kernel<false>, (const void*)amr::interp_kernel<true, 0>,
+    const void* fns[6] = {(const void*)amr::interp_kernel<false>, (const void*)amr::interp_kernel<true, 0>,
                           (const void*)amr::interp_kernel<true, 1>, (const void*)amr::interp_kernel<true, 2>,
-                          (const void*)amr::interp_kernel<true, 3>};
+                          (const void*)amr::interp_kernel<true, 3>, (const void*)amr::interp_kernel<true, 0, true>};
     cudaError_t e = cudaSuccess;
-    for (int q = 0; q < 5 && e == cudaSuccess; ++q)
+    for (int q = 0; q < 6 && e == cudaSuccess; ++q)
       e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, br.max_interp_smem);
     if (e != cudaSuccess) {
       cudaFree(it);
       cudaFree(rt);
+      cudaFree(io);
+      cudaFree(itl);
       return cuda_fail(e, "cudaFuncSetAttribute");
     }
   }
   cudaFree(p->itiles_d);
   cudaFree(p->rtiles_d);
+  cudaFree(p->incr_off_d);
+  cudaFree(p->incr_tiles_d);
   p->itiles_d = it;
   p->rtiles_d = rt;
+  p->incr_off_d = io;
+  p->incr_tiles_d = itl;
+  p->n_incr_tiles = (int)br.incr_tiles.size();
+  p->info.increment_elems = br.incr_elems;
   p->n_itiles = (int)br.interp_tiles.size();
   p->n_rtiles = (int)br.restrict_tiles.size();
   p->interp_smem = br.max_interp_smem;
@@ -293,14 +309,37 @@ amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coa
   if (p->precision == AMR_PREC_SPLIT) {
     const dim3 g(p->n_itiles), b(p->tuning.interp_threads);
     switch (p->tuning.interp_addback) {
-      case 0: amr::interp_kernel<true, 0><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine); break;
-      case 1: amr::interp_kernel<true, 1><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine); break;
-      case 3: amr::interp_kernel<true, 3><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine); break;
-      default: amr::interp_kernel<true, 2><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine); break;
+      case 0: amr::interp_kernel<true, 0><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
+      case 1: amr::interp_kernel<true, 1><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
+      case 3: amr::interp_kernel<true, 3><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
+      default: amr::interp_kernel<true, 2><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
     }
   } else
-    amr::interp_kernel<false><<<p->n_itiles, p->tuning.interp_threads, p->interp_smem, s>>>(p->items_d, p->itiles_d,
-                                                                                           p->U, coarse, fine);
+    amr::interp_kernel<false><<<p->n_itiles, p->tuning.interp_threads, p->interp_smem, s>>>(
+        p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr);
+  AMR_CUDA(cudaGetLastError());
+  return AMR_OK;
+}
+
+amr_status amr_transfer_plan_interpolate_increments(amr_transfer_plan* p, const double* coarse, float* increments,
+                                                    void* stream) {
+  amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, increments, p ? p->info.increment_elems / 2 : 0);
+  if (st != AMR_OK) return st;
+  if (p->n_itiles == 0) return AMR_OK;
+  amr::interp_kernel<true, 0, true><<<p->n_itiles, p->tuning.interp_threads, p->interp_smem, (cudaStream_t)stream>>>(
+      p->items_d, p->itiles_d, p->U, coarse, nullptr, increments, p->incr_off_d);
+  AMR_CUDA(cudaGetLastError());
+  return AMR_OK;
+}
+
+amr_status amr_transfer_plan_apply_increments(amr_transfer_plan* p, const double* coarse, const float* increments,
+                                              double* fine, void* stream) {
+  amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, fine, p ? p->fine_elems : 0);
+  if (st != AMR_OK) return st;
+  if (p->info.increment_elems > 0 && !increments) return AMR_ERR_INVALID_ARGUMENT;
+  if (p->n_incr_tiles == 0) return AMR_OK;
+  amr::apply_increments_kernel<<<p->n_incr_tiles, kThreads, 0, (cudaStream_t)stream>>>(
+      p->items_d, p->incr_tiles_d, p->incr_off_d, p->U, coarse, increments, fine);
   AMR_CUDA(cudaGetLastError());
   return AMR_OK;
 }

@@ -322,6 +322,15 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
     }
     r.interp_bytes += (int64_t)std::count(cmark.begin(), cmark.end(), 1) * U * 8;
   }
+  for (int64_t it = 0; it < desc.num_items; ++it) {
+    const amr_transfer_item& x = desc.items[it];
+    const int nsub = x.subface < 0 ? 9 : 1;
+    r.incr_off.push_back(r.incr_elems);
+    r.incr_elems += (int64_t)nsub * x.overlap * x.patch_size * x.patch_size * U;
+    for (int sl = 0; sl < nsub; ++sl)
+      for (int64_t u0 = 0; u0 < U; u0 += 128)
+        r.incr_tiles.push_back({(int32_t)it, (int16_t)sl, 0, (int16_t)u0, (int16_t)std::min<int64_t>(128, U - u0)});
+  }
   r.interp_bytes += r.interp_outputs * U * 8;
   r.restrict_bytes += r.restrict_outputs * U * 8;
   return r;

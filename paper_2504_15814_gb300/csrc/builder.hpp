@@ -57,6 +57,13 @@ struct Rows {
 Rows interpolation_rows(int sub, int slot, int p, int k, int order);
 Rows restriction_rows(int sub, int slot, int p, int k, int order);
 
+struct AdjointTile {
+  int32_t index;  // group (P^T) or item (R^T)
+  int16_t slot;   // fine face array within the item (R^T)
+  int16_t klass;  // class of the item (R^T)
+  int16_t u0, nu;
+};
+
 struct BuildResult {
   amr_status status = AMR_OK;
   std::string message;
@@ -64,6 +71,9 @@ struct BuildResult {
   int64_t interp_outputs = 0, restrict_outputs = 0;
   int64_t interp_bytes = 0, restrict_bytes = 0;
   int max_interp_smem = 0;  // bytes of dynamic shared memory the interpolation kernel needs
+  std::vector<int64_t> incr_off;          // float32 increment array offset of each item
+  std::vector<AdjointTile> incr_tiles;    // (item, fine face array, unknown chunk) of apply_increments
+  int64_t incr_elems = 0;
 };
 
 BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget);
@@ -72,12 +82,6 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget);
 // form a group and are summed in item order), R^T over each item's fine
 // face arrays.  Classes are (p, k, order, subface) with subface -1 for a whole
 // hanging face.
-struct AdjointTile {
-  int32_t index;  // group (P^T) or item (R^T)
-  int16_t slot;   // fine face array within the item (R^T)
-  int16_t klass;  // class of the item (R^T)
-  int16_t u0, nu;
-};
 struct AdjointBuild {
   std::vector<int32_t> group_ptr, group_items, item_class;
   std::vector<AdjointTile> pt_tiles, rt_tiles;

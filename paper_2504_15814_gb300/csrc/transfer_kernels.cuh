@@ -17,6 +17,7 @@
 #pragma once
 #include "amr_common.cuh"
 #include "split_arith.cuh"
+#include "builder.hpp"
 
 #include <type_traits>
 
@@ -320,11 +321,14 @@ struct Counter4 {
 // ADDBACK (split mode): which children add the increment with one float64
 // add (the rest use the integer assembly): 0 none, 1 e0 <= 0 and e1 <= 0
 // (4/9), 2 e1 <= 0 (2/3), 3 all but e0 = e1 = +1 (8/9).
-template <bool SPLIT, int ADDBACK = 2>
+// INCR (split mode): write the float32 increments (layout of
+// amr_transfer_plan_interpolate_increments) instead of float64 fine values.
+template <bool SPLIT, int ADDBACK = 2, bool INCR = false>
 __global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_transfer_item* __restrict__ items,
                                                      const Tile* __restrict__ tiles, int U,
                                                      const double* __restrict__ coarse,
-                                                     double* __restrict__ fine) {
+                                                     double* __restrict__ fine, float* __restrict__ incr,
+                                                     const int64_t* __restrict__ incr_off) {
   using SType = typename std::conditional<SPLIT, F2, double>::type;
   extern __shared__ double smem_raw[];
   SType* sm = reinterpret_cast<SType*>(smem_raw);
@@ -385,7 +389,17 @@ __global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_tr
         const F2 x = S(j, aa, bb);
         return __fadd_rn(__fsub_rn(x.hi, hc.hi), __fsub_rn(x.lo, hc.lo));
       };
-      auto emit = [&](int ii, int e0, int e1, float incr) {
+      // increment layout: item offset + (((slot k + g) p + q1) p + q0) U + u
+      float* ic_out = nullptr;
+      if constexpr (INCR)
+        ic_out = incr + incr_off[t.item] +
+                 ((((int64_t)cm.slot * k) * p + (3 * b + cm.q1_off)) * p + (3 * a + cm.q0_off)) * U + t.u0 + u;
+      auto emit = [&](int ii, int e0, int e1, float incr_v) {
+        if constexpr (INCR) {
+          ic_out[((ii * p + e1) * p + e0) * U] = (ii == 1 && e0 == 0 && e1 == 0) ? 0.f : incr_v;
+          return;
+        }
+        const float incr = incr_v;
         double v;
         if (ii == 1 && e0 == 0 && e1 == 0) v = base;
         else if ((ADDBACK == 1 && e0 <= 0 && e1 <= 0) || (ADDBACK == 2 && e1 <= 0) ||
@@ -403,6 +417,46 @@ __global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_tr
       else if (m == 2) taylor_interp_core<2, double>(S, emit, c_wt_interp, k, p, a, b, S(-1, a, b));
       else dlinear_interp_core<double>(S, emit, k, p, a, b);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fine ghost value = nearest coarse centre value + float32 increment.  One
+// thread per (ghost volume, unknown) of one fine face array; even warps add in
+// float64 (exact conversion + DADD), odd warps by TwoSum + integer assembly,
+// sharing the float64 unit and the integer pipes.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) apply_increments_kernel(const amr_transfer_item* __restrict__ items,
+                                                               const AdjointTile* __restrict__ tiles,
+                                                               const int64_t* __restrict__ incr_off, int U,
+                                                               const double* __restrict__ coarse,
+                                                               const float* __restrict__ incr,
+                                                               double* __restrict__ fine) {
+  const AdjointTile t = tiles[blockIdx.x];
+  const amr_transfer_item it = items[t.index];
+  const int p = it.patch_size, k = it.overlap;
+  const FaceFrame fr = face_frame(it.face, p, k);
+  const int64_t arr = fr.vols * U;
+  const int sub = it.subface < 0 ? t.slot : it.subface;
+  const int s0 = sub % 3, s1 = sub / 3;
+  const float* ib = incr + incr_off[t.index] + (int64_t)t.slot * k * p * p * U + t.u0;
+  double* fb = fine + it.fine_offset + (int64_t)t.slot * arr + t.u0;
+  const double* cb = coarse + it.coarse_offset + t.u0;
+  const int nu = t.nu;
+  const int ntask = nu * p * p * k;
+  const bool f64_warp = ((threadIdx.x >> 5) & 1) == 0;
+  Counter4 c;
+  c.init(threadIdx.x, blockDim.x, nu, p, p);
+  for (int e = threadIdx.x; e < ntask; e += blockDim.x, c.advance(nu, p, p)) {
+    const int u = c.u, q0 = c.x, q1 = c.y, g = c.z;
+    const int a = (s0 * p + q0) / 3, b = (s1 * p + q1) / 3;
+    const double base = __ldg(cb + frame_vol(fr, -1, a, b) * U + u);
+    const float d = __ldg(ib + ((g * p + q1) * p + q0) * U + u);
+    double v;
+    if (d == 0.f) v = base;
+    else if (f64_warp) v = __dadd_rn(base, f32_to_f64(d));
+    else v = add_back(split_f64(base), d);
+    fb[frame_vol(fr, -1 - g, q0, q1) * U + u] = v;
   }
 }
 
