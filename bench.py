@@ -403,6 +403,27 @@ def other_workloads(B, wl, stream):
     plan.close()
     del items, coarse, fine, incr
     torch.cuda.empty_cache()
+    # patch-size sweep (the paper's run time against p at halo 3, Sec. 5.3):
+    # about 2,048 * 81 / p^2 faces per p, so every point moves ~the same data
+    sweep = {}
+    for pp in (6, 9, 12, 15, 18, 24):
+        nf = max(64, int(round(2048 * 81 / (pp * pp))))
+        it9, c9, f9 = wl.uniform_batch(n_faces=nf, p=pp, k=3, U=59, order=3, config_index=1, device="cuda")
+        co9 = c9.clone()
+        row = {"faces": nf}
+        for name, order in (("taylor3", 3), ("taylor2", 2), ("dlinear", 1)):
+            it = it9.copy()
+            it["order"] = order
+            plan = B.Plan(it, 59, c9.numel(), f9.numel(), B.PREC_SPLIT)
+            info = plan.info
+            t = _time_steps(lambda: (plan.interpolate(c9, f9), plan.restrict(f9, co9)), 10, stream)
+            row[name] = {"ms_per_step": t,
+                         "value": (info["interp_outputs"] + info["restrict_outputs"]) * 59 / (t * 1e-3)}
+            plan.close()
+        sweep[f"p{pp}"] = row
+        del it9, c9, f9, co9
+    torch.cuda.empty_cache()
+    out["patch_size_sweep"] = {"workload": "k=3, U=59, split precision, ~2,048*81/p^2 hanging faces per p", **sweep}
     # uneven batch: 20,000 subface items, p in {6,9,12}, k in {2,3}, orders 1/2/3
     items, coarse, fine = wl.uneven_batch(device="cuda")
     U = 59
