@@ -34,6 +34,7 @@ from .stencils import (Unsupported, exactness_degree, lagrange_derivative_weight
                        multi_indices, window)
 
 ORDER_DLINEAR, ORDER_TAYLOR2, ORDER_TAYLOR3 = 1, 2, 3
+SCHEME_FD, SCHEME_LS = 0, 1
 
 
 def _factorial(n):
@@ -101,6 +102,100 @@ def taylor_row(centre_idx, ext, offset, order, num):
     return row
 
 
+def _stencil_support(centre_idx, ext, order):
+    """Every centre the tensor stencils of the derivatives 0 < |alpha| <= m
+    touch (the union of their windows), as index triples."""
+    pts = set()
+    for alpha in multi_indices(order):
+        if sum(alpha) == 0:
+            continue
+        axes = []
+        for d in range(3):
+            if alpha[d] == 0:
+                axes.append((centre_idx[d],))
+            else:
+                axes.append(window(centre_idx[d], 0, ext[d] - 1, exactness_degree(alpha, d, order)))
+        pts.update(product(*axes))
+    return sorted(pts)
+
+
+def _solve(M, B):
+    """Exact solution X of M X = B (Fractions, Gauss-Jordan with pivoting)."""
+    n = len(M)
+    aug = [list(M[i]) + list(B[i]) for i in range(n)]
+    for col in range(n):
+        piv = next(r for r in range(col, n) if aug[r][col] != 0)
+        aug[col], aug[piv] = aug[piv], aug[col]
+        inv = 1 / aug[col][col]
+        aug[col] = [v * inv for v in aug[col]]
+        for r in range(n):
+            if r != col and aug[r][col] != 0:
+                f = aug[r][col]
+                aug[r] = [a - f * b for a, b in zip(aug[r], aug[col])]
+    return [row[n:] for row in aug]
+
+
+@lru_cache(maxsize=None)
+def _ls_derivative_weights(rel_points, order):
+    """Least-squares fit of the derivatives D^alpha (0 < |alpha| <= m) to the
+    differences u_j - u_c at the points rel_points (offsets from the centre,
+    grid units): the basis of alpha at offset r is r^alpha / alpha!, the
+    fitted x = (A^T A)^-1 A^T (u - u_c).  Returns {alpha: [weight per point]}."""
+    alphas = [a for a in multi_indices(order) if sum(a) > 0]
+    A = []
+    for r in rel_points:
+        A.append([F_prod([Fraction(r[d]) ** a[d] / _factorial(a[d]) for d in range(3)]) for a in alphas])
+    # derivatives the points carry no information about (a zero column: e.g.
+    # tangential ones for points on one normal line) are not fitted
+    keep = [i for i in range(len(alphas)) if any(row[i] != 0 for row in A)]
+    alphas = [alphas[i] for i in keep]
+    A = [[row[i] for i in keep] for row in A]
+    n = len(alphas)
+    AtA = [[sum(A[i][p] * A[i][q] for i in range(len(A))) for q in range(n)] for p in range(n)]
+    At = [[A[i][p] for i in range(len(A))] for p in range(n)]
+    G = _solve(AtA, At)
+    return {a: G[i] for i, a in enumerate(alphas)}
+
+
+def F_prod(vals):
+    out = Fraction(1)
+    for v in vals:
+        out *= v
+    return out
+
+
+def taylor_ls_row(centre_idx, ext, offset, order, num, points=None):
+    """Row of the least-squares Taylor-m reconstruction (paper Sec. 3: a
+    polynomial fit through neighbouring centres, A x = Q^c, solved in the
+    least-squares sense) about centre_idx, evaluated at ``offset``.  The fit
+    passes through the centre value; the points are the FD stencils' support
+    (or ``points``)."""
+    c = tuple(centre_idx)
+    pts = [q for q in (points if points is not None else _stencil_support(c, ext, order)) if tuple(q) != c]
+    rel = tuple(tuple(q[d] - c[d] for d in range(3)) for q in pts)
+    G = _ls_derivative_weights(rel, order)
+    for alpha in multi_indices(order):
+        if sum(alpha) > 0 and alpha not in G:  # not fitted: its Taylor term must vanish here
+            assert F_prod([Fraction(offset[d]) ** alpha[d] for d in range(3)]) == 0
+    w = [Fraction(0)] * len(pts)
+    for alpha, g in G.items():
+        coeff = F_prod([Fraction(offset[d]) ** alpha[d] / _factorial(alpha[d]) for d in range(3)])
+        if coeff == 0:
+            continue
+        for i in range(len(pts)):
+            w[i] += coeff * g[i]
+    row = {}
+    for q, wi in zip(pts, w):
+        if wi != 0:
+            row[g_flat(ext, q)] = num(wi)
+    row[g_flat(ext, c)] = num(1 - sum(w))
+    return row
+
+
+def g_flat(ext, idx):
+    return g.flat(ext, idx)
+
+
 def _bracket_weights(coords, x, num):
     """Linear Lagrange weights {index: weight} at x from the two entries of the
     sorted coordinate list that bracket x (the two nearest at either end)."""
@@ -137,10 +232,11 @@ def _num(exact):
     return (lambda v: Fraction(v)) if exact else (lambda v: float(v))
 
 
-def interpolation_rows(face, sub, p, k, order, exact=False):
+def interpolation_rows(face, sub, p, k, order, exact=False, scheme=SCHEME_FD):
     """Rows of P for subface ``sub``: (output volumes of the fine face array,
     rows over the coarse face array).  Outputs are the fine ghost volumes in
-    flat order."""
+    flat order.  scheme: SCHEME_FD (tensor finite-difference derivatives) or
+    SCHEME_LS (least-squares fit of all derivatives at once)."""
     num = _num(exact)
     ext = g.extents(face, p, k)
     coarse_idx = g.all_indices(ext)
@@ -158,15 +254,21 @@ def interpolation_rows(face, sub, p, k, order, exact=False):
         else:
             ci = _nearest(xf, coarse_s)
             xc = coarse_x[ci]
-            row = taylor_row(coarse_idx[ci], ext, [xf[d] - xc[d] for d in range(3)], order, num)
+            off = [xf[d] - xc[d] for d in range(3)]
+            if scheme == SCHEME_LS:
+                row = taylor_ls_row(coarse_idx[ci], ext, off, order, num)
+            else:
+                row = taylor_row(coarse_idx[ci], ext, off, order, num)
         outs.append(g.flat(ext, fidx))
         rows.append(row)
     return outs, rows
 
 
-def restriction_rows(face, sub, p, k, order, exact=False):
+def restriction_rows(face, sub, p, k, order, exact=False, scheme=SCHEME_FD):
     """Rows of R for subface ``sub``: (output volumes of the coarse face array,
-    rows over subface sub's fine face array)."""
+    rows over subface sub's fine face array).  With SCHEME_LS the fit uses the
+    fine centres on the normal line through the expansion cell (the only
+    direction with a non-zero offset), inside the FD normal window."""
     num = _num(exact)
     n = g.axes(face)[0]
     side = g.coarse_side(face)
@@ -200,7 +302,17 @@ def restriction_rows(face, sub, p, k, order, exact=False):
             fi = _nearest(xC, fine_s)
             xf = fine_x[fi]
             offset = [(xC[d] - xf[d]) * 3 for d in range(3)]  # in units of h
-            row = taylor_row(fine_idx[fi], ext, offset, order, num)
+            if scheme == SCHEME_LS:
+                fidx = fine_idx[fi]
+                line = window(fidx[n], 0, ext[n] - 1, order)
+                pts = []
+                for q in line:
+                    idx = list(fidx)
+                    idx[n] = q
+                    pts.append(tuple(idx))
+                row = taylor_ls_row(fidx, ext, offset, order, num, points=pts)
+            else:
+                row = taylor_row(fine_idx[fi], ext, offset, order, num)
         outs.append(g.flat(ext, cidx))
         rows.append(row)
     return outs, rows
@@ -212,7 +324,7 @@ def _unit(d, i):
     return tuple(idx)
 
 
-def check_supported(p, k, order):
+def check_supported(p, k, order, scheme=SCHEME_FD):
     """Raise Unsupported for combinations the reading cannot serve."""
     if p % 3 != 0 or p < 3:
         raise Unsupported(f"patch size {p} must be a positive multiple of 3")
@@ -222,21 +334,23 @@ def check_supported(p, k, order):
         raise Unsupported(f"order {order}")
     if order >= 2 and (2 * k < order + 1 or p < order + 1):
         raise Unsupported(f"Taylor-{order} needs 2k >= {order + 1} and p >= {order + 1}")
+    if scheme not in (SCHEME_FD, SCHEME_LS) or (scheme == SCHEME_LS and order == ORDER_DLINEAR):
+        raise Unsupported(f"scheme {scheme} with order {order}")
 
 
 @lru_cache(maxsize=None)
-def interpolation_operator(face, sub, p, k, order):
+def interpolation_operator(face, sub, p, k, order, scheme=SCHEME_FD):
     """(output flat indices, scipy CSR matrix) of P for one subface, float64."""
-    check_supported(p, k, order)
-    outs, rows = interpolation_rows(face, sub, p, k, order)
+    check_supported(p, k, order, scheme)
+    outs, rows = interpolation_rows(face, sub, p, k, order, scheme=scheme)
     return outs, _csr(rows, g.face_array_len(p, k))
 
 
 @lru_cache(maxsize=None)
-def restriction_operator(face, sub, p, k, order):
+def restriction_operator(face, sub, p, k, order, scheme=SCHEME_FD):
     """(output flat indices, scipy CSR matrix) of R for one subface, float64."""
-    check_supported(p, k, order)
-    outs, rows = restriction_rows(face, sub, p, k, order)
+    check_supported(p, k, order, scheme)
+    outs, rows = restriction_rows(face, sub, p, k, order, scheme=scheme)
     return outs, _csr(rows, g.face_array_len(p, k))
 
 

@@ -4,7 +4,8 @@ the 1/9 block of one subface, Sec. 2 and the appendix "Code Overview").
 
 An item is any mapping with the fields
   face, subface (0..8, or -1 for all nine), patch_size p, overlap k, order,
-  coarse_offset, fine_offset
+  coarse_offset, fine_offset, and optionally scheme (0 finite-difference
+  derivatives, 1 least-squares fit)
 (offsets in float64 elements).  Its coarse face array is
 coarse[coarse_offset : coarse_offset + 2k p^2 U]; subface s's fine face array
 is fine[fine_offset + j * 2k p^2 U : ...] with j = 0 for a single-subface item
@@ -37,6 +38,14 @@ def _geom(item):
             _field(item, "order"))
 
 
+def _scheme(item):
+    """Derivative estimate of a Taylor item: 0 finite differences, 1 least squares."""
+    try:
+        return int(item["scheme"])
+    except (KeyError, ValueError, IndexError):
+        return 0
+
+
 def _arrays(item, U):
     face, p, k, order = _geom(item)
     n = g.face_array_len(p, k) * U
@@ -51,7 +60,7 @@ def interpolate(items, U, coarse, fine):
         n, co, fo = _arrays(item, U)
         X = np.asarray(coarse[co:co + n], dtype=np.float64).reshape(-1, U)
         for s, j in item_subfaces(item):
-            rows, W = interpolation_operator(face, s, p, k, order)
+            rows, W = interpolation_operator(face, s, p, k, order, _scheme(item))
             view = out[fo + j * n: fo + (j + 1) * n].reshape(-1, U)
             view[rows] = W @ X
     return out
@@ -65,7 +74,7 @@ def restrict(items, U, fine, coarse):
         n, co, fo = _arrays(item, U)
         view = out[co:co + n].reshape(-1, U)
         for s, j in item_subfaces(item):
-            rows, W = restriction_operator(face, s, p, k, order)
+            rows, W = restriction_operator(face, s, p, k, order, _scheme(item))
             X = np.asarray(fine[fo + j * n: fo + (j + 1) * n], dtype=np.float64).reshape(-1, U)
             view[rows] = W @ X
     return out
@@ -79,7 +88,7 @@ def interpolate_adjoint(items, U, g_fine, coarse_len):
         n, co, fo = _arrays(item, U)
         acc = out[co:co + n].reshape(-1, U)
         for s, j in item_subfaces(item):
-            rows, W = interpolation_operator(face, s, p, k, order)
+            rows, W = interpolation_operator(face, s, p, k, order, _scheme(item))
             G = np.asarray(g_fine[fo + j * n: fo + (j + 1) * n], dtype=np.float64).reshape(-1, U)
             acc += W.T @ G[rows]
     return out
@@ -93,7 +102,7 @@ def restrict_adjoint(items, U, g_coarse, fine_len):
         n, co, fo = _arrays(item, U)
         G = np.asarray(g_coarse[co:co + n], dtype=np.float64).reshape(-1, U)
         for s, j in item_subfaces(item):
-            rows, W = restriction_operator(face, s, p, k, order)
+            rows, W = restriction_operator(face, s, p, k, order, _scheme(item))
             acc = out[fo + j * n: fo + (j + 1) * n].reshape(-1, U)
             acc += W.T @ G[rows]
     return out
@@ -109,7 +118,7 @@ def interpolate_one(item, U, coarse, fine_index):
     j, r = divmod(rel, n)
     vol, u = divmod(r, U)
     s = j if _field(item, "subface") < 0 else _field(item, "subface")
-    rows, W = interpolation_operator(face, s, p, k, order)
+    rows, W = interpolation_operator(face, s, p, k, order, _scheme(item))
     rpos = rows.index(vol)
     lo, hi = W.indptr[rpos], W.indptr[rpos + 1]
     cols, vals = W.indices[lo:hi], W.data[lo:hi]
@@ -127,7 +136,7 @@ def restrict_one(item, U, fine, coarse_index):
     w = p // 3
     s = (idx[t0] // w) + 3 * (idx[t1] // w)
     j = s if _field(item, "subface") < 0 else 0
-    rows, W = restriction_operator(face, s, p, k, order)
+    rows, W = restriction_operator(face, s, p, k, order, _scheme(item))
     rpos = rows.index(vol)
     lo, hi = W.indptr[rpos], W.indptr[rpos + 1]
     cols, vals = W.indices[lo:hi], W.data[lo:hi]

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libamr_transfer.so")
 
 ABI_VERSION = 1
 PREC_FP64, PREC_SPLIT = 0, 1
+SCHEME_FD, SCHEME_LS = 0, 1
 ORDER_DLINEAR, ORDER_TAYLOR2, ORDER_TAYLOR3 = 1, 2, 3
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "out of memory", 4: "CUDA error",
           5: "timeout", 6: "internal error"}
@@ -28,7 +29,7 @@ class AmrError(RuntimeError):
 
 class Item(ctypes.Structure):
     _fields_ = [("face", ctypes.c_int32), ("subface", ctypes.c_int32), ("patch_size", ctypes.c_int32),
-                ("overlap", ctypes.c_int32), ("order", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("overlap", ctypes.c_int32), ("order", ctypes.c_int32), ("scheme", ctypes.c_int32),
                 ("coarse_offset", ctypes.c_int64), ("fine_offset", ctypes.c_int64)]
 
 
@@ -99,11 +100,11 @@ def _items_array(items):
     for i in range(n):
         it = items[i]
         try:
-            reserved = int(it["reserved"])
+            scheme = int(it["scheme"])
         except (KeyError, ValueError, IndexError):
-            reserved = 0
+            scheme = 0
         arr[i] = Item(int(it["face"]), int(it["subface"]), int(it["patch_size"]), int(it["overlap"]),
-                      int(it["order"]), reserved, int(it["coarse_offset"]), int(it["fine_offset"]))
+                      int(it["order"]), scheme, int(it["coarse_offset"]), int(it["fine_offset"]))
     return arr, n
 
 

@@ -35,7 +35,7 @@ import torch
 
 ITEM_DTYPE = np.dtype([
     ("face", "<i4"), ("subface", "<i4"), ("patch_size", "<i4"), ("overlap", "<i4"),
-    ("order", "<i4"), ("reserved", "<i4"), ("coarse_offset", "<i8"), ("fine_offset", "<i8"),
+    ("order", "<i4"), ("scheme", "<i4"), ("coarse_offset", "<i8"), ("fine_offset", "<i8"),
 ])
 
 SEED_BASE = 2504_15814

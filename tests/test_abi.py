@@ -58,7 +58,7 @@ def _create(items, U=4, cl=None, fl=None, abi=B.ABI_VERSION, precision=0, flags=
 
 
 def _item(**kw):
-    it = dict(face=0, subface=-1, patch_size=9, overlap=3, order=3, reserved=0, coarse_offset=0, fine_offset=0)
+    it = dict(face=0, subface=-1, patch_size=9, overlap=3, order=3, scheme=0, coarse_offset=0, fine_offset=0)
     it.update(kw)
     return it
 
@@ -67,7 +67,8 @@ def _item(**kw):
     (dict(face=6), 1), (dict(face=-1), 1), (dict(subface=9), 1), (dict(subface=-2), 1),
     (dict(order=0), 1), (dict(order=4), 1), (dict(patch_size=0), 1), (dict(overlap=0), 1),
     (dict(patch_size=8), 2), (dict(overlap=4, patch_size=12), 2), (dict(patch_size=51), 2),
-    (dict(order=2, overlap=1), 2), (dict(order=3, overlap=1), 2), (dict(reserved=1), 1),
+    (dict(order=2, overlap=1), 2), (dict(order=3, overlap=1), 2), (dict(scheme=2), 1), (dict(scheme=-1), 1),
+    (dict(scheme=1, order=1), 2),
     (dict(coarse_offset=-1), 1), (dict(fine_offset=1), 1), (dict(coarse_offset=1), 1),
 ])
 def test_invalid_items_rejected_on_host(lib, bad, status):
