@@ -42,6 +42,11 @@ extern "C" {
 
 #define AMR_TRANSFER_ABI_VERSION 1
 
+/* Plan flag: apply every item's operator as explicit sparse rows (CSR, the
+ * paper's own storage, Sec. 4.2) instead of the factorised kernels.  Items
+ * with scheme 1 always use the sparse rows. */
+#define AMR_FLAG_CSR 1
+
 typedef enum {
   AMR_OK = 0,
   AMR_ERR_INVALID_ARGUMENT = 1, /* null pointer, out-of-range field, overlapping outputs */
@@ -76,7 +81,9 @@ typedef struct {
   int32_t patch_size;    /* p: a positive multiple of 3 (better alignment, Sec. 5.3), p <= 48 */
   int32_t overlap;       /* k: 1..3; Taylor-m needs 2k >= m+1 and p >= m+1 */
   int32_t order;         /* amr_order */
-  int32_t reserved;      /* must be 0 */
+  int32_t scheme;        /* Taylor derivative estimate: 0 tensor finite-difference stencils (default),
+                            1 least-squares polynomial fit through the same centres, constrained
+                            through the centre value (Sec. 3: A x = Q^c); must be 0 for d-linear */
   int64_t coarse_offset; /* element (float64) offset of the coarse face array, 2k p^2 U elements */
   int64_t fine_offset;   /* element offset of the fine face array of the subface; for subface -1,
                             nine consecutive fine face arrays in the order s = 0..8 */
@@ -86,7 +93,7 @@ typedef struct {
   int32_t abi_version;   /* AMR_TRANSFER_ABI_VERSION */
   int32_t num_unknowns;  /* U >= 1: unknowns per volume (58 for first-order CCZ4, Sec. 2) */
   int32_t precision;     /* amr_precision */
-  int32_t flags;         /* 0 (reserved) */
+  int32_t flags;         /* 0, or AMR_FLAG_CSR */
   int64_t num_items;     /* >= 0 */
   const amr_transfer_item* items; /* host array of num_items; copied at create */
   int64_t coarse_elems;  /* float64 elements of the coarse buffer; every coarse face array must fit */
@@ -142,7 +149,8 @@ amr_status amr_transfer_plan_restrict_adjoint(amr_transfer_plan* plan, const dou
  * for fine face array s, ghost layer g (0 next to the interface), tangential
  * indices q1 (t1) and q0 (t0), unknown u.  increments holds
  * amr_transfer_plan_info.increment_elems floats; d-linear items are included
- * the same way.  Works for plans of either precision. */
+ * the same way.  Works for plans of either precision; AMR_ERR_UNSUPPORTED for
+ * plans with items on the sparse-row path (scheme 1 or AMR_FLAG_CSR). */
 amr_status amr_transfer_plan_interpolate_increments(amr_transfer_plan* plan, const double* coarse,
                                                     float* increments, void* cuda_stream);
 

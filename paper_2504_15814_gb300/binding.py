@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libamr_transfer.so")
 ABI_VERSION = 1
 PREC_FP64, PREC_SPLIT = 0, 1
 SCHEME_FD, SCHEME_LS = 0, 1
+FLAG_CSR = 1
 ORDER_DLINEAR, ORDER_TAYLOR2, ORDER_TAYLOR3 = 1, 2, 3
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "out of memory", 4: "CUDA error",
           5: "timeout", 6: "internal error"}
@@ -130,10 +131,10 @@ def _stream(stream):
 class Plan:
     """A transfer plan over a fixed item list (amr_transfer_plan_create)."""
 
-    def __init__(self, items, num_unknowns, coarse_elems, fine_elems, precision=PREC_FP64):
+    def __init__(self, items, num_unknowns, coarse_elems, fine_elems, precision=PREC_FP64, flags=0):
         self._handle = None
         arr, n = _items_array(items)
-        desc = Desc(ABI_VERSION, int(num_unknowns), int(precision), 0, n,
+        desc = Desc(ABI_VERSION, int(num_unknowns), int(precision), int(flags), n,
                     ctypes.cast(arr, ctypes.c_void_p), int(coarse_elems), int(fine_elems))
         h = ctypes.c_void_p()
         _check(lib().amr_transfer_plan_create(ctypes.byref(desc), ctypes.byref(h)), "amr_transfer_plan_create")

@@ -11,6 +11,7 @@
 
 #include "builder.hpp"
 #include "adjoint_kernels.cuh"
+#include "csr_kernels.cuh"
 #include "transfer_kernels.cuh"
 
 namespace {
@@ -103,6 +104,15 @@ struct amr_transfer_plan {
   amr::Tile* itiles_d = nullptr;
   amr::Tile* rtiles_d = nullptr;
   int n_itiles = 0, n_rtiles = 0;
+  // forward sparse rows of the items routed to the CSR kernels
+  int n_cpt = 0, n_crt = 0;
+  amr::CsrTile *cpt_d = nullptr, *crt_d = nullptr;
+  int32_t *pf_row_d = nullptr, *rf_row_d = nullptr;
+  uint32_t *pf_col_d = nullptr, *rf_col_d = nullptr, *pf_out_d = nullptr, *rf_out_d = nullptr;
+  uint32_t *pf_base_d = nullptr, *rf_base_d = nullptr;
+  double *pf_val_d = nullptr, *rf_val_d = nullptr;
+  float* pf_valf_d = nullptr;
+  int32_t flags = 0;
   int64_t* incr_off_d = nullptr;            // float32 increment offsets per item
   amr::AdjointTile* incr_tiles_d = nullptr;  // apply_increments work
   int n_incr_tiles = 0;
@@ -129,6 +139,9 @@ static void drop_graph(amr_transfer_plan* p) {
 static void free_plan(amr_transfer_plan* p) {
   if (!p) return;
   drop_graph(p);
+  void* csr[] = {p->cpt_d, p->crt_d, p->pf_row_d, p->rf_row_d, p->pf_col_d, p->rf_col_d, p->pf_out_d,
+                 p->rf_out_d, p->pf_base_d, p->rf_base_d, p->pf_val_d, p->rf_val_d, p->pf_valf_d};
+  for (void* q : csr) cudaFree(q);
   void* ptrs[] = {p->items_d, p->itiles_d, p->rtiles_d, p->incr_off_d, p->incr_tiles_d, p->pt_tiles_d, p->rt_tiles_d, p->group_ptr_d,
                   p->group_items_d, p->item_class_d, p->cls_pt_rows_d, p->cls_rt_rows_d, p->pt_row_ptr_d,
                   p->rt_row_ptr_d, p->pt_col_d, p->rt_col_d, p->pt_val_d, p->rt_val_d};
@@ -194,6 +207,7 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
   d.items = p->items_h.data();
   d.coarse_elems = p->coarse_elems;
   d.fine_elems = p->fine_elems;
+  d.flags = p->flags;
   amr::BuildResult br;
   try {
     br = amr::build_plan(d, p->tuning.interp_smem_budget);
@@ -251,8 +265,34 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
   p->info.restrict_outputs = br.restrict_outputs;
   p->info.interp_bytes = br.interp_bytes;
   p->info.restrict_bytes = br.restrict_bytes;
-  p->info.interp_launches = p->n_itiles > 0 ? 1 : 0;
-  p->info.restrict_launches = p->n_rtiles > 0 ? 1 : 0;
+  p->info.interp_launches = (p->n_itiles > 0 ? 1 : 0) + (p->n_cpt > 0 ? 1 : 0);
+  p->info.restrict_launches = (p->n_rtiles > 0 ? 1 : 0) + (p->n_crt > 0 ? 1 : 0);
+  return AMR_OK;
+}
+
+// Upload the forward sparse rows of the CSR-routed items (plan create).
+static amr_status build_csr_tables(amr_transfer_plan* p, const amr_transfer_desc& d) {
+  amr::CsrBuild cb;
+  try {
+    cb = amr::build_csr(d);
+  } catch (const std::bad_alloc&) {
+    return AMR_ERR_OUT_OF_MEMORY;
+  }
+  if (cb.ptiles.empty() && cb.rtiles.empty()) return AMR_OK;
+  std::vector<float> valf(cb.pf.val.begin(), cb.pf.val.end());
+  amr_status st;
+  if ((st = upload(cb.ptiles, &p->cpt_d)) != AMR_OK || (st = upload(cb.rtiles, &p->crt_d)) != AMR_OK ||
+      (st = upload(cb.pf.row_ptr, &p->pf_row_d)) != AMR_OK || (st = upload(cb.rf.row_ptr, &p->rf_row_d)) != AMR_OK ||
+      (st = upload(cb.pf.col, &p->pf_col_d)) != AMR_OK || (st = upload(cb.rf.col, &p->rf_col_d)) != AMR_OK ||
+      (st = upload(cb.pf.out_vol, &p->pf_out_d)) != AMR_OK || (st = upload(cb.rf.out_vol, &p->rf_out_d)) != AMR_OK ||
+      (st = upload(cb.pf.base_vol, &p->pf_base_d)) != AMR_OK ||
+      (st = upload(cb.rf.base_vol, &p->rf_base_d)) != AMR_OK || (st = upload(cb.pf.val, &p->pf_val_d)) != AMR_OK ||
+      (st = upload(cb.rf.val, &p->rf_val_d)) != AMR_OK || (st = upload(valf, &p->pf_valf_d)) != AMR_OK)
+    return st;
+  p->n_cpt = (int)cb.ptiles.size();
+  p->n_crt = (int)cb.rtiles.size();
+  p->info.interp_launches = (p->n_itiles > 0 ? 1 : 0) + (p->n_cpt > 0 ? 1 : 0);
+  p->info.restrict_launches = (p->n_rtiles > 0 ? 1 : 0) + (p->n_crt > 0 ? 1 : 0);
   return AMR_OK;
 }
 
@@ -282,7 +322,9 @@ amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_
   p->coarse_elems = desc->coarse_elems;
   p->fine_elems = desc->fine_elems;
   p->items_h.assign(desc->items, desc->items + desc->num_items);
-  if ((st = upload(p->items_h, &p->items_d)) != AMR_OK || (st = rebuild_tiles(p)) != AMR_OK) {
+  p->flags = desc->flags;
+  if ((st = upload(p->items_h, &p->items_d)) != AMR_OK || (st = rebuild_tiles(p)) != AMR_OK ||
+      (st = build_csr_tables(p, *desc)) != AMR_OK) {
     free_plan(p);
     return st;
   }
@@ -304,8 +346,20 @@ static amr_status check_call(const amr_transfer_plan* p, const void* in, int64_t
 amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coarse, double* fine, void* stream) {
   amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, fine, p ? p->fine_elems : 0);
   if (st != AMR_OK) return st;
-  if (p->n_itiles == 0) return AMR_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->n_cpt > 0) {
+    const dim3 blk(32, 8);
+    if (p->precision == AMR_PREC_SPLIT)
+      amr::csr_apply_kernel<true, true><<<p->n_cpt, blk, 0, s>>>(p->items_d, p->cpt_d, p->pf_row_d, p->pf_col_d,
+                                                                p->pf_val_d, p->pf_valf_d, p->pf_out_d, p->pf_base_d,
+                                                                p->U, coarse, fine);
+    else
+      amr::csr_apply_kernel<false, true><<<p->n_cpt, blk, 0, s>>>(p->items_d, p->cpt_d, p->pf_row_d, p->pf_col_d,
+                                                                 p->pf_val_d, p->pf_valf_d, p->pf_out_d, p->pf_base_d,
+                                                                 p->U, coarse, fine);
+    AMR_CUDA(cudaGetLastError());
+  }
+  if (p->n_itiles == 0) return AMR_OK;
   if (p->precision == AMR_PREC_SPLIT) {
     const dim3 g(p->n_itiles), b(p->tuning.interp_threads);
     switch (p->tuning.interp_addback) {
@@ -325,6 +379,7 @@ amr_status amr_transfer_plan_interpolate_increments(amr_transfer_plan* p, const 
                                                     void* stream) {
   amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, increments, p ? p->info.increment_elems / 2 : 0);
   if (st != AMR_OK) return st;
+  if (p->n_cpt > 0 || p->n_crt > 0) return AMR_ERR_UNSUPPORTED;  // increments come from the factorised kernel
   if (p->n_itiles == 0) return AMR_OK;
   amr::interp_kernel<true, 0, true><<<p->n_itiles, p->tuning.interp_threads, p->interp_smem, (cudaStream_t)stream>>>(
       p->items_d, p->itiles_d, p->U, coarse, nullptr, increments, p->incr_off_d);
@@ -337,6 +392,7 @@ amr_status amr_transfer_plan_apply_increments(amr_transfer_plan* p, const double
   amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, fine, p ? p->fine_elems : 0);
   if (st != AMR_OK) return st;
   if (p->info.increment_elems > 0 && !increments) return AMR_ERR_INVALID_ARGUMENT;
+  if (p->n_cpt > 0 || p->n_crt > 0) return AMR_ERR_UNSUPPORTED;
   if (p->n_incr_tiles == 0) return AMR_OK;
   amr::apply_increments_kernel<<<p->n_incr_tiles, kThreads, 0, (cudaStream_t)stream>>>(
       p->items_d, p->incr_tiles_d, p->incr_off_d, p->U, coarse, increments, fine);
@@ -347,8 +403,14 @@ amr_status amr_transfer_plan_apply_increments(amr_transfer_plan* p, const double
 amr_status amr_transfer_plan_restrict(amr_transfer_plan* p, const double* fine, double* coarse, void* stream) {
   amr_status st = check_call(p, fine, p ? p->fine_elems : 0, coarse, p ? p->coarse_elems : 0);
   if (st != AMR_OK) return st;
-  if (p->n_rtiles == 0) return AMR_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->n_crt > 0) {
+    amr::csr_apply_kernel<false, false><<<p->n_crt, dim3(32, 8), 0, s>>>(
+        p->items_d, p->crt_d, p->rf_row_d, p->rf_col_d, p->rf_val_d, nullptr, p->rf_out_d, p->rf_base_d, p->U, fine,
+        coarse);
+    AMR_CUDA(cudaGetLastError());
+  }
+  if (p->n_rtiles == 0) return AMR_OK;
   if (p->precision == AMR_PREC_SPLIT)
     amr::restrict_kernel<true><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(p->items_d, p->rtiles_d, p->U,
                                                                                   fine, coarse);

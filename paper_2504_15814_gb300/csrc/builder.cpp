@@ -5,7 +5,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <array>
+#include <cmath>
 #include <numeric>
+#include <set>
 
 namespace amr {
 namespace {
@@ -186,6 +189,8 @@ const Tables& tables() {
   return t;
 }
 
+bool csr_routed(const amr_transfer_desc& desc, const amr_transfer_item& x);
+
 static BuildResult fail(amr_status st, const std::string& msg) {
   BuildResult r;
   r.status = st;
@@ -200,7 +205,7 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
   if (desc.num_unknowns > 32767) return fail(AMR_ERR_UNSUPPORTED, "num_unknowns > 32767");
   if (desc.precision != AMR_PREC_FP64 && desc.precision != AMR_PREC_SPLIT)
     return fail(AMR_ERR_INVALID_ARGUMENT, "unknown precision");
-  if (desc.flags != 0) return fail(AMR_ERR_INVALID_ARGUMENT, "flags must be 0");
+  if (desc.flags & ~AMR_FLAG_CSR) return fail(AMR_ERR_INVALID_ARGUMENT, "unknown flags");
   if (desc.num_items < 0 || (desc.num_items > 0 && desc.items == nullptr))
     return fail(AMR_ERR_INVALID_ARGUMENT, "bad item list");
   if (desc.num_items > (int64_t)1 << 30) return fail(AMR_ERR_UNSUPPORTED, "too many items");
@@ -222,7 +227,8 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
     if (x.face < 0 || x.face > 5) return bad(AMR_ERR_INVALID_ARGUMENT, "face not in 0..5");
     if (x.subface < -1 || x.subface > 8) return bad(AMR_ERR_INVALID_ARGUMENT, "subface not in -1..8");
     if (x.order < 1 || x.order > 3) return bad(AMR_ERR_INVALID_ARGUMENT, "order not in 1..3");
-    if (x.reserved != 0) return bad(AMR_ERR_INVALID_ARGUMENT, "reserved must be 0");
+    if (x.scheme != 0 && x.scheme != 1) return bad(AMR_ERR_INVALID_ARGUMENT, "scheme not in 0..1");
+    if (x.scheme == 1 && x.order == AMR_ORDER_DLINEAR) return bad(AMR_ERR_UNSUPPORTED, "least-squares scheme needs a Taylor order");
     if (x.patch_size < 1 || x.overlap < 1) return bad(AMR_ERR_INVALID_ARGUMENT, "p and k must be positive");
     if (x.overlap > x.patch_size) return bad(AMR_ERR_INVALID_ARGUMENT, "k > p");
     if (x.patch_size % 3 != 0) return bad(AMR_ERR_UNSUPPORTED, "p must be a multiple of 3");
@@ -297,15 +303,16 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
     const amr_transfer_item& x = desc.items[it];
     const int p = x.patch_size, k = x.overlap, m = x.order, w = p / 3;
     std::vector<char> cmark((size_t)2 * k * p * p, 0);
-    if (x.subface < 0) {
+    const bool fused = !csr_routed(desc, x);  // factorised kernels (else the CSR kernels)
+    if (x.subface < 0 && fused) {
       add_interp_tiles(it, -1, -1, 0, p, 0, p, p, k, m);
       add_restrict_tiles(it, -1, -1, 0, p, 0, p);
     }
     for (int sl = 0; sl < (x.subface < 0 ? 9 : 1); ++sl) {
       const int sub = x.subface < 0 ? sl : x.subface;
       const int s0 = sub % 3, s1 = sub / 3;
-      if (x.subface >= 0) add_interp_tiles(it, sub, 0, s0 * w, (s0 + 1) * w, s1 * w, (s1 + 1) * w, p, k, m);
-      if (x.subface >= 0) add_restrict_tiles(it, sub, 0, s0 * w, (s0 + 1) * w, s1 * w, (s1 + 1) * w);
+      if (x.subface >= 0 && fused) add_interp_tiles(it, sub, 0, s0 * w, (s0 + 1) * w, s1 * w, (s1 + 1) * w, p, k, m);
+      if (x.subface >= 0 && fused) add_restrict_tiles(it, sub, 0, s0 * w, (s0 + 1) * w, s1 * w, (s1 + 1) * w);
       for (int b = s1 * w; b < (s1 + 1) * w; ++b)
         for (int a = s0 * w; a < (s0 + 1) * w; ++a) mark_interp(cmark, p, k, m, a, b);
       auto key = std::make_tuple(p, k, m, sub);
@@ -394,9 +401,96 @@ std::vector<std::pair<int, double>> dlin_axis(int c, int n, int e) {
   return {{c - 1, -1.0 / 3.0}, {c, 4.0 / 3.0}};
 }
 
+// Least-squares Taylor weights (scheme 1): for the points `rel` (offsets from
+// the expansion centre, grid units, centre excluded), the fitted derivatives
+// x = (A^T A)^-1 A^T (u - u_c) with basis r^alpha / alpha!, evaluated in
+// Taylor's formula at offset `off`; returns the weight of each point (the
+// centre gets 1 - sum).  Derivatives the points carry no information about
+// (zero columns) are not fitted; their terms vanish at `off` by construction.
+std::vector<double> ls_taylor_weights(const std::vector<std::array<int, 3>>& rel, int order,
+                                      const std::array<long double, 3>& off) {
+  std::vector<std::array<int, 3>> alphas;
+  for (int x = 0; x <= order; ++x)
+    for (int y = 0; x + y <= order; ++y)
+      for (int z = 0; x + y + z <= order; ++z)
+        if (x + y + z > 0) alphas.push_back({x, y, z});
+  auto fact = [](int n) { long double f = 1; for (int q = 2; q <= n; ++q) f *= q; return f; };
+  auto basis = [&](const std::array<int, 3>& r, const std::array<int, 3>& a) {
+    long double v = 1;
+    for (int d = 0; d < 3; ++d) v *= std::pow((long double)r[d], a[d]) / fact(a[d]);
+    return v;
+  };
+  std::vector<std::array<int, 3>> used;
+  for (auto& a : alphas) {
+    bool any = false;
+    for (auto& r : rel) any |= basis(r, a) != 0;
+    if (any) used.push_back(a);
+  }
+  const int n = (int)used.size(), m = (int)rel.size();
+  // augmented normal equations [A^T A | A^T]
+  std::vector<std::vector<long double>> aug(n, std::vector<long double>(n + m, 0));
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j)
+      for (int q = 0; q < m; ++q) aug[i][j] += basis(rel[q], used[i]) * basis(rel[q], used[j]);
+    for (int q = 0; q < m; ++q) aug[i][n + q] = basis(rel[q], used[i]);
+  }
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(aug[r][col]) > std::fabs(aug[piv][col])) piv = r;
+    std::swap(aug[col], aug[piv]);
+    const long double inv = 1 / aug[col][col];
+    for (auto& v : aug[col]) v *= inv;
+    for (int r = 0; r < n; ++r)
+      if (r != col && aug[r][col] != 0) {
+        const long double f = aug[r][col];
+        for (int c = 0; c < n + m; ++c) aug[r][c] -= f * aug[col][c];
+      }
+  }
+  std::vector<double> w(m, 0.0);
+  for (int i = 0; i < n; ++i) {
+    long double coeff = 1;
+    for (int d = 0; d < 3; ++d) coeff *= std::pow(off[d], used[i][d]) / fact(used[i][d]);
+    if (coeff == 0) continue;
+    for (int q = 0; q < m; ++q) w[q] += (double)(coeff * aug[i][n + q]);
+  }
+  return w;
+}
+
+// Support of the finite-difference stencils of Taylor-m about centre c on
+// the index box [lo, hi] (pure lines, mixed planes, and for m = 3 the box).
+std::vector<std::array<int, 3>> stencil_support(const int c[3], const int lo[3], const int hi[3], int order) {
+  std::set<std::array<int, 3>> pts;
+  int s, l;
+  for (int d = 0; d < 3; ++d) {
+    stencil_window(c[d], lo[d], hi[d], pure_exactness(order), s, l);
+    for (int q = s; q < s + l; ++q) {
+      std::array<int, 3> x{c[0], c[1], c[2]};
+      x[d] = q;
+      pts.insert(x);
+    }
+  }
+  int ms[3], ml[3];
+  for (int d = 0; d < 3; ++d) stencil_window(c[d], lo[d], hi[d], mixed_exactness(order), ms[d], ml[d]);
+  for (int d = 0; d < 3; ++d)
+    for (int e = d + 1; e < 3; ++e)
+      for (int qd = ms[d]; qd < ms[d] + ml[d]; ++qd)
+        for (int qe = ms[e]; qe < ms[e] + ml[e]; ++qe) {
+          std::array<int, 3> x{c[0], c[1], c[2]};
+          x[d] = qd;
+          x[e] = qe;
+          pts.insert(x);
+        }
+  if (order == 3)
+    for (int q0 = ms[0]; q0 < ms[0] + ml[0]; ++q0)
+      for (int q1 = ms[1]; q1 < ms[1] + ml[1]; ++q1)
+        for (int q2 = ms[2]; q2 < ms[2] + ml[2]; ++q2) pts.insert({q0, q1, q2});
+  return std::vector<std::array<int, 3>>(pts.begin(), pts.end());
+}
+
 }  // namespace
 
-Rows interpolation_rows(int sub, int slot, int p, int k, int order) {
+Rows interpolation_rows(int sub, int slot, int p, int k, int order, int scheme) {
   Rows r;
   const int s0 = sub % 3, s1 = sub / 3;
   for (int i = -k; i <= -1; ++i)
@@ -414,6 +508,19 @@ Rows interpolation_rows(int sub, int slot, int p, int k, int order) {
           for (auto& [jn, w_n] : wn)
             for (auto& [ja, w_a] : dlin_axis(a, p, e0))
               for (auto& [jb, w_b] : dlin_axis(b, p, e1)) row[pack_vol(0, jn + k, jb, ja)] += w_n * w_a * w_b;
+        } else if (scheme == 1) {
+          const int c[3] = {-1, a, b}, lo[3] = {-k, 0, 0}, hi[3] = {k - 1, p - 1, p - 1};
+          std::vector<std::array<int, 3>> rel;
+          for (auto& x : stencil_support(c, lo, hi, order))
+            if (x[0] != c[0] || x[1] != c[1] || x[2] != c[2]) rel.push_back({x[0] - c[0], x[1] - c[1], x[2] - c[2]});
+          const std::array<long double, 3> off{en / 3.0L, e0 / 3.0L, e1 / 3.0L};
+          const std::vector<double> w = ls_taylor_weights(rel, order, off);
+          double sum = 0.0;
+          for (size_t q = 0; q < rel.size(); ++q) {
+            row[pack_vol(0, c[0] + rel[q][0] + k, c[2] + rel[q][2], c[1] + rel[q][1])] += w[q];
+            sum += w[q];
+          }
+          row[pack_vol(0, -1 + k, b, a)] += 1.0 - sum;
         } else {
           add_taylor_interp_row(row, p, k, order, a, b, en, e0, e1);
         }
@@ -423,7 +530,7 @@ Rows interpolation_rows(int sub, int slot, int p, int k, int order) {
   return r;
 }
 
-Rows restriction_rows(int sub, int slot, int p, int k, int order) {
+Rows restriction_rows(int sub, int slot, int p, int k, int order, int scheme) {
   Rows r;
   const Tables& t = tables();
   const int s0 = sub % 3, s1 = sub / 3, w = p / 3;
@@ -442,6 +549,20 @@ Rows restriction_rows(int sub, int slot, int p, int k, int order) {
           }
         } else if (j == 0) {
           row[pack_vol(slot, 1 + k, q1, q0)] = 1.0;
+        } else if (scheme == 1) {
+          int s, L;
+          stencil_window(k - 1, -k, k - 1, pure_exactness(order), s, L);
+          std::vector<std::array<int, 3>> rel;
+          for (int i = s; i < s + L; ++i)
+            if (i != k - 1) rel.push_back({i - (k - 1), 0, 0});
+          const std::array<long double, 3> off{(long double)(3 * j + 2 - k), 0.0L, 0.0L};
+          const std::vector<double> w = ls_taylor_weights(rel, order, off);
+          double sum = 0.0;
+          for (size_t q = 0; q < rel.size(); ++q) {
+            row[pack_vol(slot, k - 1 + rel[q][0] + k, q1, q0)] += w[q];
+            sum += w[q];
+          }
+          row[pack_vol(slot, k - 1 + k, q1, q0)] += 1.0 - sum;
         } else {
           int s, L;
           stencil_window(k - 1, -k, k - 1, pure_exactness(order), s, L);
@@ -490,7 +611,7 @@ AdjointBuild build_adjoint(const amr_transfer_desc& desc) {
   std::map<int64_t, std::vector<int32_t>> groups;
   for (int64_t it = 0; it < desc.num_items; ++it) {
     const amr_transfer_item& x = desc.items[it];
-    auto key = std::make_tuple(x.patch_size, x.overlap, x.order, x.subface);
+    auto key = std::make_tuple(x.patch_size, x.overlap, x.order * 2 + x.scheme, x.subface);
     auto f = classes.find(key);
     if (f == classes.end()) {
       const int id = (int)classes.size();
@@ -500,8 +621,8 @@ AdjointBuild build_adjoint(const amr_transfer_desc& desc) {
       const int nsub = x.subface < 0 ? 9 : 1;
       for (int sl = 0; sl < nsub; ++sl) {
         const int sub = x.subface < 0 ? sl : x.subface;
-        pblocks.push_back(interpolation_rows(sub, sl, p, k, m));
-        rblocks.push_back(restriction_rows(sub, sl, p, k, m));
+        pblocks.push_back(interpolation_rows(sub, sl, p, k, m, x.scheme));
+        rblocks.push_back(restriction_rows(sub, sl, p, k, m, x.scheme));
       }
       const int arr = 2 * k * p * p;
       append_transpose(ab.pt, ab.cls_pt_rows, pblocks, arr, p, k);
@@ -526,6 +647,76 @@ AdjointBuild build_adjoint(const amr_transfer_desc& desc) {
                                (int16_t)std::min<int64_t>(128, U - u0)});
   }
   return ab;
+}
+
+}  // namespace amr
+
+// ---------------------------------------------------------------------------
+// Forward sparse rows for the CSR kernels.
+// ---------------------------------------------------------------------------
+namespace amr {
+
+bool csr_routed(const amr_transfer_desc& desc, const amr_transfer_item& x) {
+  return x.scheme == 1 || (desc.flags & AMR_FLAG_CSR) != 0;
+}
+
+CsrBuild build_csr(const amr_transfer_desc& desc) {
+  CsrBuild cb;
+  cb.pf.row_ptr.push_back(0);
+  cb.rf.row_ptr.push_back(0);
+  struct ClassRows { int32_t p0, np, r0, nr; };
+  std::map<std::tuple<int, int, int, int>, ClassRows> classes;
+  auto append = [](CsrFwd& f, const Rows& rows, auto base_of) {
+    for (size_t i = 0; i < rows.rows.size(); ++i) {
+      for (auto& [c, w] : rows.rows[i]) {
+        f.col.push_back(c);
+        f.val.push_back(w);
+      }
+      f.row_ptr.push_back((int32_t)f.col.size());
+      f.out_vol.push_back(rows.out_vol[i]);
+      f.base_vol.push_back(base_of(rows.out_vol[i]));
+    }
+  };
+  for (int64_t it = 0; it < desc.num_items; ++it) {
+    const amr_transfer_item& x = desc.items[it];
+    cb.routed.push_back(csr_routed(desc, x) ? 1 : 0);
+    if (!cb.routed.back()) continue;
+    const int p = x.patch_size, k = x.overlap, m = x.order;
+    auto key = std::make_tuple(p, k, m * 2 + x.scheme, x.subface);
+    auto f = classes.find(key);
+    if (f == classes.end()) {
+      ClassRows cr{(int32_t)cb.pf.out_vol.size(), 0, (int32_t)cb.rf.out_vol.size(), 0};
+      const int nsub = x.subface < 0 ? 9 : 1;
+      for (int sl = 0; sl < nsub; ++sl) {
+        const int sub = x.subface < 0 ? sl : x.subface;
+        const int s0 = sub % 3, s1 = sub / 3;
+        // interpolation: the base is the coarse centre (layer -1) nearest to the fine volume
+        append(cb.pf, interpolation_rows(sub, sl, p, k, m, x.scheme), [&](uint32_t v) {
+          const int q1 = (int)((v >> 6) & 63u), q0 = (int)(v & 63u);
+          return pack_vol(0, k - 1, (s1 * p + q1) / 3, (s0 * p + q0) / 3);
+        });
+        // restriction: the base is the fine cell the expansion is about
+        append(cb.rf, restriction_rows(sub, sl, p, k, m, x.scheme), [&](uint32_t v) {
+          const int lk = (int)((v >> 12) & 7u), b = (int)((v >> 6) & 63u), a = (int)(v & 63u);
+          const int j = lk - k;
+          const int i = m == AMR_ORDER_DLINEAR ? 0 : std::min(3 * j + 1, k - 1);
+          return pack_vol(sl, i + k, 3 * b + 1 - s1 * p, 3 * a + 1 - s0 * p);
+        });
+      }
+      cr.np = (int32_t)cb.pf.out_vol.size() - cr.p0;
+      cr.nr = (int32_t)cb.rf.out_vol.size() - cr.r0;
+      f = classes.emplace(key, cr).first;
+    }
+    const ClassRows& cr = f->second;
+    const int RT = 32;  // rows per tile
+    for (int r = 0; r < cr.np; r += RT)
+      cb.ptiles.push_back({(int32_t)it, cr.p0 + r, std::min(RT, cr.np - r), 0, 0});
+    for (int r = 0; r < cr.nr; r += RT)
+      cb.rtiles.push_back({(int32_t)it, cr.r0 + r, std::min(RT, cr.nr - r), 0, 0});
+  }
+  cb.p_nnz = (int64_t)cb.pf.col.size();
+  cb.r_nnz = (int64_t)cb.rf.col.size();
+  return cb;
 }
 
 }  // namespace amr

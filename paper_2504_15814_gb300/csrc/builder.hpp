@@ -54,8 +54,31 @@ struct Rows {
   std::vector<uint32_t> out_vol;
   std::vector<std::vector<std::pair<uint32_t, double>>> rows;
 };
-Rows interpolation_rows(int sub, int slot, int p, int k, int order);
-Rows restriction_rows(int sub, int slot, int p, int k, int order);
+Rows interpolation_rows(int sub, int slot, int p, int k, int order, int scheme = 0);
+Rows restriction_rows(int sub, int slot, int p, int k, int order, int scheme = 0);
+
+// Forward sparse rows of the items routed to the CSR kernels (scheme 1, or
+// every item with AMR_FLAG_CSR), per face class, for P and for R: row r of a
+// class writes out_vol[r] from sum_e val[e] in[col[e]]; base_vol[r] is the
+// input volume the split path takes differences against (the nearest input
+// centre).
+struct CsrFwd {
+  std::vector<int32_t> row_ptr;  // absolute into col / val
+  std::vector<uint32_t> col, out_vol, base_vol;
+  std::vector<double> val;
+};
+struct CsrTile {
+  int32_t item;
+  int32_t row0, nrow;  // absolute rows of the concatenated class tables
+  int16_t u0, nu;
+};
+struct CsrBuild {
+  CsrFwd pf, rf;                       // interpolation and restriction rows
+  std::vector<CsrTile> ptiles, rtiles;
+  std::vector<char> routed;            // per item: 1 if it uses the CSR kernels
+  int64_t p_nnz = 0, r_nnz = 0;
+};
+CsrBuild build_csr(const amr_transfer_desc& desc);
 
 struct AdjointTile {
   int32_t index;  // group (P^T) or item (R^T)

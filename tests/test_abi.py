@@ -84,7 +84,7 @@ def test_bad_descriptor(lib):
     assert st == 1 and h.value is None
     st, h = _create([_item()], precision=7)
     assert st == 1
-    st, h = _create([_item()], flags=1)
+    st, h = _create([_item()], flags=2)
     assert st == 1
     assert lib.amr_transfer_plan_create(None, None) == 1
     assert lib.amr_transfer_plan_destroy(None) == 0

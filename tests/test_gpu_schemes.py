@@ -1,0 +1,89 @@
+"""GPU parity of the least-squares scheme (paper Sec. 3 read as a
+least-squares polynomial fit) and of the sparse-row (CSR) kernels that also
+serve every item under AMR_FLAG_CSR, against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import transfer as tr
+from paper_2504_15814_gb300 import binding as B
+from paper_2504_15814_gb300 import workloads as wl
+
+from .parity import gpu_interpolate, gpu_restrict, normwise_errors, record, written_masks
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(orders, schemes, U=7, seed=3):
+    n = len(orders)
+    faces = [i % 6 for i in range(n)]
+    subs = [-1 if i % 3 == 0 else (i * 5) % 9 for i in range(n)]
+    ps = [9 if i % 2 == 0 else 6 for i in range(n)]
+    ks = [3 if i % 4 < 2 else 2 for i in range(n)]
+    items, cl, fl = wl.make_items(faces, subs, ps, ks, orders, U)
+    items["scheme"] = schemes
+    rng = np.random.Generator(np.random.PCG64(wl.SEED_BASE + 300 + seed))
+    coarse, fine = wl.sample_buffers(items, U, cl, fl, wl.SmoothField(U, rng), wl.origins_in_box(n, rng))
+    return items, coarse.numpy(), fine.numpy()
+
+
+def _check(items, U, c, f, precision, tol_i, tol_r, flags=0, tag=""):
+    plan = B.Plan(items, U, len(c), len(f), precision, flags)
+    fm, cm = written_masks(items, U, len(c), len(f))
+    f_gpu = gpu_interpolate(plan, c, f)
+    assert np.array_equal(f_gpu[~fm], f[~fm])
+    e_i = normwise_errors(items, U, f_gpu, tr.interpolate(items, U, c, f), fm, "fine")[0]
+    c_gpu = gpu_restrict(plan, f, c)
+    assert np.array_equal(c_gpu[~cm], c[~cm])
+    e_r = normwise_errors(items, U, c_gpu, tr.restrict(items, U, f, c), cm, "coarse")[0]
+    record(test="schemes", tag=tag, precision=precision, interp=e_i, restrict=e_r)
+    assert e_i <= tol_i and e_r <= tol_r, (e_i, e_r)
+    return plan
+
+
+@pytest.mark.parametrize("precision,tol_i", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6)])
+@pytest.mark.parametrize("order", [2, 3])
+def test_least_squares_items(order, precision, tol_i):
+    items, c, f = _batch([order] * 12, [1] * 12)
+    _check(items, 7, c, f, precision, tol_i, 1e-12, tag=f"ls{order}")
+
+
+def test_mixed_fd_and_ls_items_in_one_plan():
+    orders = [3, 2, 3, 1, 2, 3, 1, 3, 2, 2, 3, 1]
+    schemes = [1, 0, 0, 0, 1, 1, 0, 0, 0, 1, 1, 0]
+    items, c, f = _batch(orders, schemes, seed=8)
+    _check(items, 7, c, f, B.PREC_FP64, 1e-12, 1e-12, tag="mixed")
+
+
+@pytest.mark.parametrize("precision,tol_i", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6)])
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_csr_flag_reproduces_factorised_operators(order, precision, tol_i):
+    items, c, f = _batch([order] * 12, [0] * 12, seed=11)
+    plan = _check(items, 7, c, f, precision, tol_i, 1e-12, flags=B.FLAG_CSR, tag=f"csr{order}")
+    assert plan.info["interp_launches"] == 1
+
+
+def test_least_squares_adjoint_matches_oracle_transposes():
+    U = 5
+    items, c, f = _batch([3, 2, 3, 2, 3, 3], [1] * 6, U=U, seed=21)
+    plan = B.Plan(items, U, len(c), len(f), B.PREC_FP64)
+    rng = np.random.default_rng(4)
+    gf, gc = rng.standard_normal(len(f)), rng.standard_normal(len(c))
+    oc = torch.empty(len(c), dtype=torch.float64, device="cuda")
+    of = torch.empty(len(f), dtype=torch.float64, device="cuda")
+    plan.interpolate_adjoint(torch.as_tensor(gf).cuda(), oc)
+    plan.restrict_adjoint(torch.as_tensor(gc).cuda(), of)
+    torch.cuda.synchronize()
+    ref_c = tr.interpolate_adjoint(items, U, gf, len(c))
+    ref_f = tr.restrict_adjoint(items, U, gc, len(f))
+    rel = lambda a, b: np.abs(a - b).max() / np.abs(b).max()
+    assert rel(oc.cpu().numpy(), ref_c) <= 1e-12
+    assert rel(of.cpu().numpy(), ref_f) <= 1e-12
+
+
+def test_increments_rejected_on_sparse_row_plans():
+    items, c, f = _batch([3] * 3, [1] * 3)
+    plan = B.Plan(items, 7, len(c), len(f), B.PREC_SPLIT)
+    incr = torch.empty(plan.info["increment_elems"], dtype=torch.float32, device="cuda")
+    with pytest.raises(B.AmrError):
+        plan.interpolate_increments(torch.as_tensor(c).cuda(), incr)
