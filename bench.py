@@ -403,6 +403,24 @@ def other_workloads(B, wl, stream):
     plan.close()
     del items, coarse, fine, incr
     torch.cuda.empty_cache()
+    # least-squares scheme and the sparse-row (CSR, the paper's storage) path
+    # on the uniform batch, Taylor-3
+    items, coarse, fine = wl.uniform_batch(n_faces=2048, U=59, order=3, config_index=1, device="cuda")
+    co = coarse.clone()
+    rows = {}
+    for name, scheme, flags in (("least_squares", 1, 0), ("csr_finite_difference", 0, B.FLAG_CSR)):
+        it = items.copy()
+        it["scheme"] = scheme
+        for prec_name, prec in (("split", B.PREC_SPLIT), ("fp64", B.PREC_FP64)):
+            plan = B.Plan(it, 59, coarse.numel(), fine.numel(), prec, flags)
+            info = plan.info
+            t = _time_steps(lambda: (plan.interpolate(coarse, fine), plan.restrict(fine, co)), 5, stream)
+            rows[f"{name}_{prec_name}"] = {"ms_per_step": t,
+                                           "value": (info["interp_outputs"] + info["restrict_outputs"]) * 59 / (t * 1e-3)}
+            plan.close()
+    out["taylor3_variants"] = {"workload": "2,048 hanging faces, p=9, k=3, U=59, Taylor-3", **rows}
+    del items, coarse, fine, co
+    torch.cuda.empty_cache()
     # patch-size sweep (the paper's run time against p at halo 3, Sec. 5.3):
     # about 2,048 * 81 / p^2 faces per p, so every point moves ~the same data
     sweep = {}
