@@ -17,7 +17,10 @@ Conventions used throughout this repository:
   (i_n - k + 1/2) * spacing, the interface being at 0; tangential index i_t
   of the coarse array sits at (i_t + 1/2) * H.
 * Subface s = s0 + 3 s1 (s0 along t0, s1 along t1) is the fine patch whose
-  tangential index i_t sits at (s_t * p + i_t + 1/2) * h.
+  tangential index i_t sits at (s_t * p + i_t + 1/2) * h.  Coarse cell a
+  covers fine global indices 3a .. 3a+2 and its centre coincides with fine
+  3a + 1; when p is not a multiple of 3 a subface boundary can cut a coarse
+  cell, which then belongs to the subface holding 3a + 1.
 * Coordinates here are in units of H, in the face's own frame (origin at the
   face corner on the interface plane).
 """
@@ -92,19 +95,24 @@ def fine_ghost_indices(face, p, k):
     return [idx for idx in all_indices(ext) if (idx[n] - k + Fraction(1, 2)) * side > 0]
 
 
+def owner_subface_index(a, p):
+    """Subface index (along one tangential axis) owning coarse cell a: the one
+    holding the fine cell 3a + 1 that coincides with the coarse centre."""
+    return (3 * a + 1) // p
+
+
 def coarse_halo_indices(face, p, k, sub):
-    """Coarse face-array volumes on the fine side that lie over subface sub:
-    written by restriction from that subface."""
+    """Coarse face-array volumes on the fine side whose centre coincides with
+    a fine centre of subface sub: written by restriction from that subface."""
     n, t0, t1 = axes(face)
     side = coarse_side(face)
     s0, s1 = subface_pos(face, sub)
-    w = p // 3
     ext = extents(face, p, k)
     out = []
     for idx in all_indices(ext):
         if (idx[n] - k + Fraction(1, 2)) * side > 0:
             continue
-        if idx[t0] // w == s0 and idx[t1] // w == s1:
+        if owner_subface_index(idx[t0], p) == s0 and owner_subface_index(idx[t1], p) == s1:
             out.append(idx)
     return out
 

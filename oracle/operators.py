@@ -293,10 +293,14 @@ def restriction_rows(face, sub, p, k, order, exact=False, scheme=SCHEME_FD):
                     lw = _ls_line_weights([coords[i] for i in own], xC[d], num)
                     axis_w.append(dict(zip(own, lw)))
                 else:
-                    # fine volumes whose centres lie inside the coarse volume
+                    # least-squares line through the subface's fine volumes
+                    # inside the coarse volume, at its centre: the average of
+                    # all three, or the coincident one if a subface boundary
+                    # cuts the coarse volume (p not a multiple of 3)
                     inside = [i for i in range(ext[d])
                               if abs(fine_x[g.flat(ext, _unit(d, i))][d] - xC[d]) < Fraction(1, 2)]
-                    axis_w.append({i: num(Fraction(1, len(inside))) for i in inside})
+                    xs = [fine_x[g.flat(ext, _unit(d, i))][d] for i in inside]
+                    axis_w.append(dict(zip(inside, _ls_line_weights(xs, xC[d], num))))
             row = _outer_row(ext, axis_w, num)
         else:
             fi = _nearest(xC, fine_s)
@@ -326,8 +330,8 @@ def _unit(d, i):
 
 def check_supported(p, k, order, scheme=SCHEME_FD):
     """Raise Unsupported for combinations the reading cannot serve."""
-    if p % 3 != 0 or p < 3:
-        raise Unsupported(f"patch size {p} must be a positive multiple of 3")
+    if p < 3:
+        raise Unsupported(f"patch size {p} must be at least 3")
     if k < 1 or k > p:
         raise Unsupported(f"overlap {k} must satisfy 1 <= k <= p")
     if order not in (ORDER_DLINEAR, ORDER_TAYLOR2, ORDER_TAYLOR3):

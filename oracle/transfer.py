@@ -133,8 +133,7 @@ def restrict_one(item, U, fine, coarse_index):
     ext = g.extents(face, p, k)
     idx = (vol % ext[0], (vol // ext[0]) % ext[1], vol // (ext[0] * ext[1]))
     _, t0, t1 = g.axes(face)
-    w = p // 3
-    s = (idx[t0] // w) + 3 * (idx[t1] // w)
+    s = g.owner_subface_index(idx[t0], p) + 3 * g.owner_subface_index(idx[t1], p)
     j = s if _field(item, "subface") < 0 else 0
     rows, W = restriction_operator(face, s, p, k, order, _scheme(item))
     rpos = rows.index(vol)
