@@ -78,7 +78,11 @@ typedef enum {
 typedef struct {
   int32_t face;          /* 0..5, see the layout note above */
   int32_t subface;       /* 0..8 = s0 + 3 s1, or -1 for all nine subfaces */
-  int32_t patch_size;    /* p: a positive multiple of 3 (better alignment, Sec. 5.3), p <= 48 */
+  int32_t patch_size;    /* p: 1..48 (at least m+1 for Taylor-m).  Coarse volume a covers fine
+                            global tangential indices 3a..3a+2 and coincides with 3a+1; for p
+                            not a multiple of 3 (Sec. 5.3 notes multiples align better) a
+                            subface boundary can cut a coarse volume, which the subface holding
+                            3a+1 restricts (d-linear: injected along the cut axis) */
   int32_t overlap;       /* k: 1..3; Taylor-m needs 2k >= m+1 and p >= m+1 */
   int32_t order;         /* amr_order */
   int32_t scheme;        /* Taylor derivative estimate: 0 tensor finite-difference stencils (default),

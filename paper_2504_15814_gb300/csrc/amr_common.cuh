@@ -12,7 +12,10 @@
 //   * coarse centre of layer j at (j + 1/2) H, fine layer i at (i + 1/2) h,
 //     h = H / 3; coarse tangential a at (a + 1/2) H, fine global tangential
 //     g = s_t p + q at (g + 1/2) h, so fine g coincides with coarse g / 3
-//     exactly when g = 3a + 1.
+//     exactly when g = 3a + 1;
+//   * coarse a covers fine 3a .. 3a+2.  When p is not a multiple of 3 a
+//     subface boundary can cut a coarse volume: its children then lie in two
+//     fine face arrays, and it is restricted by the subface holding 3a + 1.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -90,6 +93,20 @@ __host__ __device__ inline void stencil_window(int c, int lo, int hi, int E, int
 // mixed derivatives (exact to degree <= 2 along each axis: 3 points).
 __host__ __device__ inline int pure_exactness(int order) { return order; }
 __host__ __device__ inline int mixed_exactness(int order) { return order == 3 ? 2 : 1; }
+
+// Coarse tangential indices [lo, hi) restricted by subface position s: those
+// whose coincident fine index 3a + 1 lies in [s p, s p + p).
+__host__ __device__ inline void owned_range(int s, int p, int& lo, int& hi) {
+  lo = (s * p + 1) / 3;
+  hi = (s * p + p + 1) / 3;
+}
+
+// Coarse tangential indices [lo, hi) with at least one fine child in subface
+// position s (interpolation sources of that subface).
+__host__ __device__ inline void covering_range(int s, int p, int& lo, int& hi) {
+  lo = (s * p) / 3;
+  hi = (s * p + p - 1) / 3 + 1;
+}
 
 struct IRange { int lo, hi; };
 

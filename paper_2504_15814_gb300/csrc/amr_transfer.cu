@@ -104,6 +104,7 @@ struct amr_transfer_plan {
   amr::Tile* itiles_d = nullptr;
   amr::Tile* rtiles_d = nullptr;
   int n_itiles = 0, n_rtiles = 0;
+  int n_cut_itiles = 0;  // the last n_cut_itiles interpolation tiles run the CUT kernel variant
   // forward sparse rows of the items routed to the CSR kernels
   int n_cpt = 0, n_crt = 0;
   amr::CsrTile *cpt_d = nullptr, *crt_d = nullptr;
@@ -197,6 +198,11 @@ const char* amr_status_string(amr_status s) {
 
 const char* amr_last_cuda_error(void) { return g_cuda_error.c_str(); }
 
+// Kernel launches of one interpolate call.
+static int interp_launch_count(const amr_transfer_plan* p) {
+  return (p->n_itiles - p->n_cut_itiles > 0 ? 1 : 0) + (p->n_cut_itiles > 0 ? 1 : 0) + (p->n_cpt > 0 ? 1 : 0);
+}
+
 // (Re)build the forward tiles of a plan for its tuning (synchronous).
 static amr_status rebuild_tiles(amr_transfer_plan* p) {
   amr_transfer_desc d{};
@@ -233,11 +239,14 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
     return st;
   }
   if (br.max_interp_smem > 48 * 1024) {
-    const void* fns[6] = {(const void*)amr::interp_kernel<false>, (const void*)amr::interp_kernel<true, 0>,
+    const void* fns[9] = {(const void*)amr::interp_kernel<false>, (const void*)amr::interp_kernel<true, 0>,
                           (const void*)amr::interp_kernel<true, 1>, (const void*)amr::interp_kernel<true, 2>,
-                          (const void*)amr::interp_kernel<true, 3>, (const void*)amr::interp_kernel<true, 0, true>};
+                          (const void*)amr::interp_kernel<true, 3>, (const void*)amr::interp_kernel<true, 0, true>,
+                          (const void*)amr::interp_kernel<false, 2, false, true>,
+                          (const void*)amr::interp_kernel<true, 2, false, true>,
+                          (const void*)amr::interp_kernel<true, 0, true, true>};
     cudaError_t e = cudaSuccess;
-    for (int q = 0; q < 6 && e == cudaSuccess; ++q)
+    for (int q = 0; q < 9 && e == cudaSuccess; ++q)
       e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, br.max_interp_smem);
     if (e != cudaSuccess) {
       cudaFree(it);
@@ -258,6 +267,7 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
   p->n_incr_tiles = (int)br.incr_tiles.size();
   p->info.increment_elems = br.incr_elems;
   p->n_itiles = (int)br.interp_tiles.size();
+  p->n_cut_itiles = (int)br.n_cut_interp_tiles;
   p->n_rtiles = (int)br.restrict_tiles.size();
   p->interp_smem = br.max_interp_smem;
   p->info.num_items = d.num_items;
@@ -265,7 +275,7 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
   p->info.restrict_outputs = br.restrict_outputs;
   p->info.interp_bytes = br.interp_bytes;
   p->info.restrict_bytes = br.restrict_bytes;
-  p->info.interp_launches = (p->n_itiles > 0 ? 1 : 0) + (p->n_cpt > 0 ? 1 : 0);
+  p->info.interp_launches = interp_launch_count(p);
   p->info.restrict_launches = (p->n_rtiles > 0 ? 1 : 0) + (p->n_crt > 0 ? 1 : 0);
   return AMR_OK;
 }
@@ -291,7 +301,7 @@ static amr_status build_csr_tables(amr_transfer_plan* p, const amr_transfer_desc
     return st;
   p->n_cpt = (int)cb.ptiles.size();
   p->n_crt = (int)cb.rtiles.size();
-  p->info.interp_launches = (p->n_itiles > 0 ? 1 : 0) + (p->n_cpt > 0 ? 1 : 0);
+  p->info.interp_launches = interp_launch_count(p);
   p->info.restrict_launches = (p->n_rtiles > 0 ? 1 : 0) + (p->n_crt > 0 ? 1 : 0);
   return AMR_OK;
 }
@@ -359,19 +369,31 @@ amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coa
                                                                  p->U, coarse, fine);
     AMR_CUDA(cudaGetLastError());
   }
-  if (p->n_itiles == 0) return AMR_OK;
-  if (p->precision == AMR_PREC_SPLIT) {
-    const dim3 g(p->n_itiles), b(p->tuning.interp_threads);
-    switch (p->tuning.interp_addback) {
-      case 0: amr::interp_kernel<true, 0><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
-      case 1: amr::interp_kernel<true, 1><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
-      case 3: amr::interp_kernel<true, 3><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
-      default: amr::interp_kernel<true, 2><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
+  const int n_reg = p->n_itiles - p->n_cut_itiles;
+  const dim3 b(p->tuning.interp_threads);
+  if (n_reg > 0) {
+    const dim3 g(n_reg);
+    if (p->precision == AMR_PREC_SPLIT) {
+      switch (p->tuning.interp_addback) {
+        case 0: amr::interp_kernel<true, 0><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
+        case 1: amr::interp_kernel<true, 1><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
+        case 3: amr::interp_kernel<true, 3><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
+        default: amr::interp_kernel<true, 2><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
+      }
+    } else {
+      amr::interp_kernel<false><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr);
     }
-  } else
-    amr::interp_kernel<false><<<p->n_itiles, p->tuning.interp_threads, p->interp_smem, s>>>(
-        p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr);
-  AMR_CUDA(cudaGetLastError());
+    AMR_CUDA(cudaGetLastError());
+  }
+  if (p->n_cut_itiles > 0) {
+    const dim3 g(p->n_cut_itiles);
+    const amr::Tile* ct = p->itiles_d + n_reg;
+    if (p->precision == AMR_PREC_SPLIT)
+      amr::interp_kernel<true, 2, false, true><<<g, b, p->interp_smem, s>>>(p->items_d, ct, p->U, coarse, fine, nullptr, nullptr);
+    else
+      amr::interp_kernel<false, 2, false, true><<<g, b, p->interp_smem, s>>>(p->items_d, ct, p->U, coarse, fine, nullptr, nullptr);
+    AMR_CUDA(cudaGetLastError());
+  }
   return AMR_OK;
 }
 
@@ -380,10 +402,18 @@ amr_status amr_transfer_plan_interpolate_increments(amr_transfer_plan* p, const 
   amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, increments, p ? p->info.increment_elems / 2 : 0);
   if (st != AMR_OK) return st;
   if (p->n_cpt > 0 || p->n_crt > 0) return AMR_ERR_UNSUPPORTED;  // increments come from the factorised kernel
-  if (p->n_itiles == 0) return AMR_OK;
-  amr::interp_kernel<true, 0, true><<<p->n_itiles, p->tuning.interp_threads, p->interp_smem, (cudaStream_t)stream>>>(
-      p->items_d, p->itiles_d, p->U, coarse, nullptr, increments, p->incr_off_d);
-  AMR_CUDA(cudaGetLastError());
+  const int n_reg = p->n_itiles - p->n_cut_itiles;
+  if (n_reg > 0) {
+    amr::interp_kernel<true, 0, true><<<n_reg, p->tuning.interp_threads, p->interp_smem, (cudaStream_t)stream>>>(
+        p->items_d, p->itiles_d, p->U, coarse, nullptr, increments, p->incr_off_d);
+    AMR_CUDA(cudaGetLastError());
+  }
+  if (p->n_cut_itiles > 0) {
+    amr::interp_kernel<true, 0, true, true><<<p->n_cut_itiles, p->tuning.interp_threads, p->interp_smem,
+                                              (cudaStream_t)stream>>>(p->items_d, p->itiles_d + n_reg, p->U, coarse,
+                                                                      nullptr, increments, p->incr_off_d);
+    AMR_CUDA(cudaGetLastError());
+  }
   return AMR_OK;
 }
 

@@ -168,10 +168,13 @@ void mark_interp(std::vector<char>& m, int p, int k, int order, int a, int b) {
 void mark_restrict(std::vector<char>& m, int p, int k, int order, int q0, int q1) {
   auto mark = [&](int i, int aa, int bb) { m[((size_t)(i + k) * p + bb) * p + aa] = 1; };
   if (order == AMR_ORDER_DLINEAR) {
+    // a coarse volume cut by the subface boundary (coincident fine column on
+    // the array's edge) is injected along that axis
+    const int da0 = (q0 == 0 || q0 == p - 1) ? 0 : 1, db0 = (q1 == 0 || q1 == p - 1) ? 0 : 1;
     const int ilo = (k == 1) ? -1 : 0, ihi = (k == 1) ? 0 : k - 1;
     for (int i = ilo; i <= ihi; ++i)
-      for (int db = -1; db <= 1; ++db)
-        for (int da = -1; da <= 1; ++da) mark(i, q0 + da, q1 + db);
+      for (int db = -db0; db <= db0; ++db)
+        for (int da = -da0; da <= da0; ++da) mark(i, q0 + da, q1 + db);
     return;
   }
   if (k >= 2) mark(1, q0, q1);  // injection
@@ -231,7 +234,6 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
     if (x.scheme == 1 && x.order == AMR_ORDER_DLINEAR) return bad(AMR_ERR_UNSUPPORTED, "least-squares scheme needs a Taylor order");
     if (x.patch_size < 1 || x.overlap < 1) return bad(AMR_ERR_INVALID_ARGUMENT, "p and k must be positive");
     if (x.overlap > x.patch_size) return bad(AMR_ERR_INVALID_ARGUMENT, "k > p");
-    if (x.patch_size % 3 != 0) return bad(AMR_ERR_UNSUPPORTED, "p must be a multiple of 3");
     if (x.patch_size > 48) return bad(AMR_ERR_UNSUPPORTED, "p > 48");
     if (x.overlap > 3) return bad(AMR_ERR_UNSUPPORTED, "k > 3");
     if (x.order >= 2 && (2 * x.overlap < x.order + 1 || x.patch_size < x.order + 1))
@@ -265,7 +267,12 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
 
   // Tiles and byte counts.
   const int TMAX = 12;
+  // interpolation tiles of items whose patch size is not a multiple of 3
+  // (children of one coarse centre may lie in two fine face arrays) go to a
+  // second list, appended after the others and run by their own kernel variant
+  std::vector<Tile> cut_tiles;
   auto add_interp_tiles = [&](int64_t it, int sub, int slot, int alo, int ahi, int blo, int bhi, int p, int k, int m) {
+    std::vector<Tile>& dst = p % 3 ? cut_tiles : r.interp_tiles;
     for (int a0 = alo; a0 < ahi; a0 += TMAX)
       for (int b0 = blo; b0 < bhi; b0 += TMAX) {
         const int na = std::min(TMAX, ahi - a0), nb = std::min(TMAX, bhi - b0);
@@ -280,7 +287,7 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
           t.item = (int32_t)it; t.sub = (int8_t)sub; t.slot = (int8_t)slot;
           t.na = (int8_t)na; t.nb = (int8_t)nb; t.a0 = (int16_t)a0; t.b0 = (int16_t)b0;
           t.u0 = (int16_t)(c * nu); t.nu = (int16_t)std::min<int64_t>(nu, U - c * nu);
-          r.interp_tiles.push_back(t);
+          dst.push_back(t);
           r.max_interp_smem = std::max<int>(r.max_interp_smem, (int)(vols * t.nu * 8));
         }
       }
@@ -301,7 +308,7 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
   std::map<std::tuple<int, int, int, int>, int64_t> ref_cache;  // (p,k,order,sub) -> restriction references
   for (int64_t it = 0; it < desc.num_items; ++it) {
     const amr_transfer_item& x = desc.items[it];
-    const int p = x.patch_size, k = x.overlap, m = x.order, w = p / 3;
+    const int p = x.patch_size, k = x.overlap, m = x.order;
     std::vector<char> cmark((size_t)2 * k * p * p, 0);
     const bool fused = !csr_routed(desc, x);  // factorised kernels (else the CSR kernels)
     if (x.subface < 0 && fused) {
@@ -311,21 +318,26 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
     for (int sl = 0; sl < (x.subface < 0 ? 9 : 1); ++sl) {
       const int sub = x.subface < 0 ? sl : x.subface;
       const int s0 = sub % 3, s1 = sub / 3;
-      if (x.subface >= 0 && fused) add_interp_tiles(it, sub, 0, s0 * w, (s0 + 1) * w, s1 * w, (s1 + 1) * w, p, k, m);
-      if (x.subface >= 0 && fused) add_restrict_tiles(it, sub, 0, s0 * w, (s0 + 1) * w, s1 * w, (s1 + 1) * w);
-      for (int b = s1 * w; b < (s1 + 1) * w; ++b)
-        for (int a = s0 * w; a < (s0 + 1) * w; ++a) mark_interp(cmark, p, k, m, a, b);
+      int ca0, ca1, cb0, cb1, oa0, oa1, ob0, ob1;  // covering and owned coarse ranges
+      covering_range(s0, p, ca0, ca1);
+      covering_range(s1, p, cb0, cb1);
+      owned_range(s0, p, oa0, oa1);
+      owned_range(s1, p, ob0, ob1);
+      if (x.subface >= 0 && fused) add_interp_tiles(it, sub, 0, ca0, ca1, cb0, cb1, p, k, m);
+      if (x.subface >= 0 && fused) add_restrict_tiles(it, sub, 0, oa0, oa1, ob0, ob1);
+      for (int b = cb0; b < cb1; ++b)
+        for (int a = ca0; a < ca1; ++a) mark_interp(cmark, p, k, m, a, b);
       auto key = std::make_tuple(p, k, m, sub);
       auto f = ref_cache.find(key);
       if (f == ref_cache.end()) {
         std::vector<char> fmark((size_t)2 * k * p * p, 0);
-        for (int b = s1 * w; b < (s1 + 1) * w; ++b)
-          for (int a = s0 * w; a < (s0 + 1) * w; ++a) mark_restrict(fmark, p, k, m, 3 * a + 1 - s0 * p, 3 * b + 1 - s1 * p);
+        for (int b = ob0; b < ob1; ++b)
+          for (int a = oa0; a < oa1; ++a) mark_restrict(fmark, p, k, m, 3 * a + 1 - s0 * p, 3 * b + 1 - s1 * p);
         f = ref_cache.emplace(key, (int64_t)std::count(fmark.begin(), fmark.end(), 1)).first;
       }
       r.restrict_bytes += f->second * U * 8;
       r.interp_outputs += (int64_t)k * p * p;
-      r.restrict_outputs += (int64_t)k * w * w;
+      r.restrict_outputs += (int64_t)k * (oa1 - oa0) * (ob1 - ob0);
     }
     r.interp_bytes += (int64_t)std::count(cmark.begin(), cmark.end(), 1) * U * 8;
   }
@@ -340,6 +352,8 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
   }
   r.interp_bytes += r.interp_outputs * U * 8;
   r.restrict_bytes += r.restrict_outputs * U * 8;
+  r.n_cut_interp_tiles = (int64_t)cut_tiles.size();
+  r.interp_tiles.insert(r.interp_tiles.end(), cut_tiles.begin(), cut_tiles.end());
   return r;
 }
 
@@ -533,19 +547,27 @@ Rows interpolation_rows(int sub, int slot, int p, int k, int order, int scheme) 
 Rows restriction_rows(int sub, int slot, int p, int k, int order, int scheme) {
   Rows r;
   const Tables& t = tables();
-  const int s0 = sub % 3, s1 = sub / 3, w = p / 3;
+  const int s0 = sub % 3, s1 = sub / 3;
+  int a_lo, a_hi, b_lo, b_hi;
+  owned_range(s0, p, a_lo, a_hi);
+  owned_range(s1, p, b_lo, b_hi);
   for (int j = 0; j < k; ++j)
-    for (int b = s1 * w; b < (s1 + 1) * w; ++b)
-      for (int a = s0 * w; a < (s0 + 1) * w; ++a) {
+    for (int b = b_lo; b < b_hi; ++b)
+      for (int a = a_lo; a < a_hi; ++a) {
         const int q0 = 3 * a + 1 - s0 * p, q1 = 3 * b + 1 - s1 * p;
         Row row;
         if (order == AMR_ORDER_DLINEAR) {
+          // tangential: the average of the 3 fine volumes inside the coarse
+          // volume, or injection of the coincident one along an axis where
+          // the subface boundary cuts the coarse volume
+          const int da0 = (q0 == 0 || q0 == p - 1) ? 0 : 1, db0 = (q1 == 0 || q1 == p - 1) ? 0 : 1;
+          const double nt = (double)((2 * da0 + 1) * (2 * db0 + 1));
           const int nl = k == 1 ? 2 : k;
           for (int sl = 0; sl < nl; ++sl) {
             const int i = k == 1 ? sl - 1 : sl;
-            const double wl = t.ls[ls_index(k, j, sl)] / 9.0;
-            for (int db = -1; db <= 1; ++db)
-              for (int da = -1; da <= 1; ++da) row[pack_vol(slot, i + k, q1 + db, q0 + da)] += wl;
+            const double wl = t.ls[ls_index(k, j, sl)] / nt;
+            for (int db = -db0; db <= db0; ++db)
+              for (int da = -da0; da <= da0; ++da) row[pack_vol(slot, i + k, q1 + db, q0 + da)] += wl;
           }
         } else if (j == 0) {
           row[pack_vol(slot, 1 + k, q1, q0)] = 1.0;

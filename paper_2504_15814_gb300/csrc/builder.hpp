@@ -91,6 +91,7 @@ struct BuildResult {
   amr_status status = AMR_OK;
   std::string message;
   std::vector<Tile> interp_tiles, restrict_tiles;
+  int64_t n_cut_interp_tiles = 0;  // the last ones of interp_tiles: items with p not a multiple of 3
   int64_t interp_outputs = 0, restrict_outputs = 0;
   int64_t interp_bytes = 0, restrict_bytes = 0;
   int max_interp_smem = 0;  // bytes of dynamic shared memory the interpolation kernel needs

@@ -288,6 +288,29 @@ __device__ __forceinline__ ChildMap child_map(const Tile& t, int p, int a, int b
   return m;
 }
 
+// Patch sizes that are not a multiple of 3: placement of the children
+// e = -1, 0, +1 of a coarse centre along one tangential axis, relative to the
+// centre child (fine global g = 3a + 1, local q in the subface array it is
+// addressed in).  In a whole-face tile the centre child's own array is used
+// and an outer child on the far side of a subface boundary steps into the
+// neighbouring array (slot_stride apart, local index p - 1 or 0).  In a
+// one-subface tile every child outside [0, p) is dropped.
+struct CutAxis {
+  long long off_m, off_p;
+  bool v_m, v_z, v_p;
+};
+__device__ __forceinline__ CutAxis cut_axis(bool whole, int q, int p, long long gs, long long slot_stride) {
+  CutAxis c;
+  c.off_m = (whole && q == 0) ? (long long)(p - 1) * gs - slot_stride : -gs;
+  c.off_p = (whole && q == p - 1) ? slot_stride - (long long)(p - 1) * gs : gs;
+  c.v_m = whole || (q >= 1 && q <= p);
+  c.v_z = whole || (q >= 0 && q < p);
+  c.v_p = whole || (q >= -1 && q <= p - 2);
+  return c;
+}
+__device__ __forceinline__ long long cut_off(const CutAxis& c, int e) { return e < 0 ? c.off_m : (e > 0 ? c.off_p : 0); }
+__device__ __forceinline__ bool cut_valid(const CutAxis& c, int e) { return e < 0 ? c.v_m : (e > 0 ? c.v_p : c.v_z); }
+
 // Mixed-radix counter over (u, x, y, z) with radices (nu, NX, NY, -): walks
 // e, e + step, ... without integer divisions in the loop.
 struct Counter4 {
@@ -323,7 +346,9 @@ struct Counter4 {
 // (4/9), 2 e1 <= 0 (2/3), 3 all but e0 = e1 = +1 (8/9).
 // INCR (split mode): write the float32 increments (layout of
 // amr_transfer_plan_interpolate_increments) instead of float64 fine values.
-template <bool SPLIT, int ADDBACK = 2, bool INCR = false>
+// CUT: tiles of items whose patch size is not a multiple of 3 (children of
+// one centre may lie in two fine face arrays, see CutAxis).
+template <bool SPLIT, int ADDBACK = 2, bool INCR = false, bool CUT = false>
 __global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_transfer_item* __restrict__ items,
                                                      const Tile* __restrict__ tiles, int U,
                                                      const double* __restrict__ coarse,
@@ -369,19 +394,46 @@ __global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_tr
   }
   __syncthreads();
   const int64_t arr = fr.vols * U;
+  const float inv_p = 1.0f / (float)p;
   const int SA = nu, SB = NA * nu, SJ = NB * NA * nu;
   const int ntask = t.na * t.nb * nu;
   Counter4 c;
   c.init(threadIdx.x, blockDim.x, nu, t.na, t.nb);
   for (int e = threadIdx.x; e < ntask; e += blockDim.x, c.advance(nu, t.na, t.nb)) {
     const int u = c.u, a = t.a0 + c.x, b = t.b0 + c.y;
-    const ChildMap cm = child_map(t, p, a, b);
+    ChildMap cm;
+    CutAxis ca, cbx;
+    if constexpr (CUT) {
+      // the centre child's subface: 3a + 1 = s p + q, 0 <= q < p in a whole-face tile
+      int s0 = t.sub % 3, s1 = t.sub / 3;
+      cm.slot = t.slot;
+      if (t.sub < 0) {
+        s0 = (int)(__fmaf_rn((float)a, 3.f, 1.5f) * inv_p);
+        s1 = (int)(__fmaf_rn((float)b, 3.f, 1.5f) * inv_p);
+        cm.slot = s0 + 3 * s1;
+      }
+      cm.q0_off = 1 - s0 * p;
+      cm.q1_off = 1 - s1 * p;
+      // strides of the written layout: fine face arrays, or the increment array
+      const long long g0s = INCR ? (long long)U : gs_a, g1s = INCR ? (long long)p * U : gs_b;
+      const long long slot_s = INCR ? (long long)k * p * p * U : arr;
+      ca = cut_axis(t.sub < 0, 3 * a + cm.q0_off, p, g0s, slot_s);
+      cbx = cut_axis(t.sub < 0, 3 * b + cm.q1_off, p, g1s, 3 * slot_s);
+    } else {
+      cm = child_map(t, p, a, b);
+    }
     // child (fine layer -1, tangential offsets 0, 0) of this centre and unknown
     double* fc = fine + it.fine_offset + (int64_t)cm.slot * arr +
                  frame_vol(fr, -1, 3 * a + cm.q0_off, 3 * b + cm.q1_off) * U + t.u0 + u;
     const int ic = ((-1 - rn.lo) * NB + (b - rb.lo)) * NA * nu + (a - ra.lo) * nu + u;
     auto S = [&](int j, int aa, int bb) -> SType { return sm[ic + (j + 1) * SJ + (bb - b) * SB + (aa - a) * SA]; };
-    auto store = [&](int ii, int e0, int e1, double v) { fc[-ii * gs_n + e0 * gs_a + e1 * gs_b] = v; };
+    auto store = [&](int ii, int e0, int e1, double v) {
+      if constexpr (CUT) {
+        if (cut_valid(ca, e0) && cut_valid(cbx, e1)) fc[-ii * gs_n + cut_off(ca, e0) + cut_off(cbx, e1)] = v;
+      } else {
+        fc[-ii * gs_n + e0 * gs_a + e1 * gs_b] = v;
+      }
+    };
     if constexpr (SPLIT) {
       const F2 hc = sm[ic];
       const double base = __ldg(cb + frame_vol(fr, -1, a, b) * U + u);
@@ -396,7 +448,12 @@ __global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_tr
                  ((((int64_t)cm.slot * k) * p + (3 * b + cm.q1_off)) * p + (3 * a + cm.q0_off)) * U + t.u0 + u;
       auto emit = [&](int ii, int e0, int e1, float incr_v) {
         if constexpr (INCR) {
-          ic_out[((ii * p + e1) * p + e0) * U] = (ii == 1 && e0 == 0 && e1 == 0) ? 0.f : incr_v;
+          const float w = (ii == 1 && e0 == 0 && e1 == 0) ? 0.f : incr_v;
+          if constexpr (CUT) {
+            if (cut_valid(ca, e0) && cut_valid(cbx, e1)) ic_out[(long long)ii * p * p * U + cut_off(ca, e0) + cut_off(cbx, e1)] = w;
+          } else {
+            ic_out[((ii * p + e1) * p + e0) * U] = w;
+          }
           return;
         }
         const float incr = incr_v;
@@ -586,21 +643,24 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
   const int64_t arr = fr.vols * U;
   const int gs_n = (int)fr.s_n * U, gs_a = (int)fr.s_t0 * U, gs_b = (int)fr.s_t1 * U;
   double* cb = coarse + it.coarse_offset + t.u0;
-  const float inv_w = 3.0f / (float)p;
+  const float inv_p = 1.0f / (float)p;
   const int nu = t.nu;
   const int ntask = t.na * t.nb * nu;
-  // fine column (layer 0) and coarse halo column (layer 0) of a task
-  auto columns = [&](const Counter4& c, const double*& fcol, double*& ccol) {
+  // fine column (layer 0) and coarse halo column (layer 0) of a task; q0, q1:
+  // local tangential index of the coincident fine column
+  auto columns = [&](const Counter4& c, const double*& fcol, double*& ccol, int& q0, int& q1) {
     const int u = c.u, a = t.a0 + c.x, b = t.b0 + c.y;
     int s0, s1, slot;
     if (t.sub >= 0) {
       s0 = t.sub % 3; s1 = t.sub / 3; slot = t.slot;
-    } else {  // whole-face tile: (a + 1/2) / w is never within 1/32 of an integer
-      s0 = (int)(((float)a + 0.5f) * inv_w);
-      s1 = (int)(((float)b + 0.5f) * inv_w);
+    } else {  // whole-face tile: the owner holds fine 3a + 1, and (3a + 3/2) / p
+              // is never within 1/(2p) of an integer
+      s0 = (int)(__fmaf_rn((float)a, 3.f, 1.5f) * inv_p);
+      s1 = (int)(__fmaf_rn((float)b, 3.f, 1.5f) * inv_p);
       slot = s0 + 3 * s1;
     }
-    const int q0 = 3 * a + 1 - s0 * p, q1 = 3 * b + 1 - s1 * p;
+    q0 = 3 * a + 1 - s0 * p;
+    q1 = 3 * b + 1 - s1 * p;
     fcol = fine + it.fine_offset + (int64_t)slot * arr + t.u0 + frame_vol(fr, 0, q0, q1) * U + u;
     ccol = cb + frame_vol(fr, 0, a, b) * U + u;
   };
@@ -620,7 +680,8 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const double* fcol;
-        columns(c, fcol, ccol[r]);
+        int q0, q1;
+        columns(c, fcol, ccol[r], q0, q1);
         const bool ok = e0 + r * (int)blockDim.x < ntask;
 #pragma unroll
         for (int i = 0; i < 5; ++i) v[r][i] = (ok && i < L) ? __ldg(fcol + (s + i) * gs_n) : 0.0;
@@ -657,8 +718,13 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
     for (int e = threadIdx.x; e < ntask; e += blockDim.x, c.advance(nu, t.na, t.nb)) {
       const double* fcol;
       double* ccol;
-      columns(c, fcol, ccol);
-      auto F = [&](int i, int da, int db) -> double { return __ldg(fcol + i * gs_n + da * gs_a + db * gs_b); };
+      int q0, q1;
+      columns(c, fcol, ccol, q0, q1);
+      // a coarse volume cut by a subface boundary (p not a multiple of 3; the
+      // coincident column on the array's edge) is injected along that axis:
+      // the three tangential reads collapse onto the coincident column
+      const int ga = (q0 == 0 || q0 == p - 1) ? 0 : gs_a, gb = (q1 == 0 || q1 == p - 1) ? 0 : gs_b;
+      auto F = [&](int i, int da, int db) -> double { return __ldg(fcol + i * gs_n + da * ga + db * gb); };
       auto C = [&](int j, double v) { ccol[j * gs_n] = v; };
       if (SPLIT) dlinear_restrict_split(F, C, k);
       else dlinear_restrict_f64(F, C, k);

@@ -66,7 +66,7 @@ def _item(**kw):
 @pytest.mark.parametrize("bad,status", [
     (dict(face=6), 1), (dict(face=-1), 1), (dict(subface=9), 1), (dict(subface=-2), 1),
     (dict(order=0), 1), (dict(order=4), 1), (dict(patch_size=0), 1), (dict(overlap=0), 1),
-    (dict(patch_size=8), 2), (dict(overlap=4, patch_size=12), 2), (dict(patch_size=51), 2),
+    (dict(patch_size=3), 2), (dict(overlap=4, patch_size=12), 2), (dict(patch_size=51), 2),
     (dict(order=2, overlap=1), 2), (dict(order=3, overlap=1), 2), (dict(scheme=2), 1), (dict(scheme=-1), 1),
     (dict(scheme=1, order=1), 2),
     (dict(coarse_offset=-1), 1), (dict(fine_offset=1), 1), (dict(coarse_offset=1), 1),
