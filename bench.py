@@ -314,7 +314,8 @@ def main():
                        "faces_per_gpu": args.faces, "p": P, "k": K, "U": U, "order": 3,
                        "precision": args.precision, "parallelism": f"dp{world}" if world > 1 else "single GPU",
                        "tuning": tuning,
-                       "l2": "inputs (4.7 GB) larger than L2, no flush"},
+                       "l2": f"inputs ({(coarse.numel() + fine.numel()) * 8 / 1e9:.1f} GB) larger than L2, "
+                             "no flush"},
             "roofline": roofline, "clocks": clocks,
             "gpu_launches": args.steps * (info["interp_launches"] + info["restrict_launches"])}
 
@@ -421,10 +422,11 @@ def other_workloads(B, wl, stream):
     out["taylor3_variants"] = {"workload": "2,048 hanging faces, p=9, k=3, U=59, Taylor-3", **rows}
     del items, coarse, fine, co
     torch.cuda.empty_cache()
-    # patch-size sweep (the paper's run time against p at halo 3, Sec. 5.3):
-    # about 2,048 * 81 / p^2 faces per p, so every point moves ~the same data
+    # patch-size sweep (the paper's run time against p at halo 3, Sec. 5.3,
+    # where multiples of 3 align coarse and fine cells better): about
+    # 2,048 * 81 / p^2 faces per p, so every point moves ~the same data
     sweep = {}
-    for pp in (6, 9, 12, 15, 18, 24):
+    for pp in (6, 8, 9, 10, 12, 15, 16, 18, 24):
         nf = max(64, int(round(2048 * 81 / (pp * pp))))
         it9, c9, f9 = wl.uniform_batch(n_faces=nf, p=pp, k=3, U=59, order=3, config_index=1, device="cuda")
         co9 = c9.clone()

@@ -179,18 +179,25 @@ typedef struct {
 
 amr_status amr_transfer_plan_get_info(const amr_transfer_plan* plan, amr_transfer_plan_info* info);
 
-/* Launch shapes of a plan.  interp_threads / restrict_threads: CTA size of
- * the two kernels (32..256, a multiple of 32); interp_smem_budget: bytes of
- * shared memory an interpolation tile may stage (4096..200704; it sets how
- * many unknowns one tile carries); interp_addback (split precision only,
- * 0..3): share of the interpolated children whose float64 result is formed
- * by one float64 add instead of float32 TwoSum + integer assembly -- 0 none,
- * 1 four ninths, 2 two thirds (default), 3 eight ninths. */
+/* Launch shapes of a plan.  interp_threads: CTA size of the interpolation
+ * kernel (a multiple of 32; up to 384 in split precision, 256 in float64);
+ * restrict_threads: CTA size of the restriction kernel (32..256, a multiple
+ * of 32); interp_smem_budget: bytes of shared memory an interpolation tile
+ * may stage (4096..200704; it sets how many unknowns one tile carries);
+ * interp_addback (split precision only, 0..3): share of the interpolated
+ * children whose float64 result is formed by one float64 add instead of
+ * float32 TwoSum + integer assembly -- 0 none, 1 four ninths, 2 two thirds
+ * (default), 3 eight ninths; interp_lanes: how interpolation threads map to
+ * (coarse centre, unknown) tasks -- 0 packs them densely with the unknown
+ * fastest (default), 32 gives every coarse centre one warp whose lanes are
+ * its unknowns (a tile then carries at most 32 unknowns), so that a warp
+ * never straddles two centres. */
 typedef struct {
   int32_t interp_threads;
   int32_t interp_smem_budget;
   int32_t restrict_threads;
   int32_t interp_addback;
+  int32_t interp_lanes;
 } amr_transfer_tuning;
 
 amr_status amr_transfer_plan_get_tuning(const amr_transfer_plan* plan, amr_transfer_tuning* out);

@@ -49,7 +49,8 @@ class PlanInfo(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("interp_threads", ctypes.c_int32), ("interp_smem_budget", ctypes.c_int32),
-                ("restrict_threads", ctypes.c_int32), ("interp_addback", ctypes.c_int32)]
+                ("restrict_threads", ctypes.c_int32), ("interp_addback", ctypes.c_int32),
+                ("interp_lanes", ctypes.c_int32)]
 
 
 ENTRY_POINTS = {
@@ -205,8 +206,9 @@ class Plan:
         _check(lib().amr_transfer_plan_get_tuning(self._handle, ctypes.byref(out)), "get_tuning")
         return {name: getattr(out, name) for name, _ in Tuning._fields_}
 
-    def set_tuning(self, interp_threads, interp_smem_budget, restrict_threads, interp_addback=2):
-        t = Tuning(int(interp_threads), int(interp_smem_budget), int(restrict_threads), int(interp_addback))
+    def set_tuning(self, interp_threads, interp_smem_budget, restrict_threads, interp_addback=2, interp_lanes=0):
+        t = Tuning(int(interp_threads), int(interp_smem_budget), int(restrict_threads), int(interp_addback),
+                   int(interp_lanes))
         _check(lib().amr_transfer_plan_set_tuning(self._handle, ctypes.byref(t)), "set_tuning")
 
     def autotune(self, coarse, fine, coarse_out, stream=None):

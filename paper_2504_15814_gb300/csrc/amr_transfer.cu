@@ -119,7 +119,7 @@ struct amr_transfer_plan {
   int n_incr_tiles = 0;
   int interp_smem = 0;  // bytes of dynamic shared memory per interpolation CTA
   amr_transfer_plan_info info{};
-  amr_transfer_tuning tuning{kThreads, kSmemBudget, kThreads, 2};
+  amr_transfer_tuning tuning{kThreads, kSmemBudget, kThreads, 2, 0};
   cudaGraphExec_t step_exec = nullptr;
   // adjoint tables, built on the first adjoint call
   std::vector<amr_transfer_item> items_h;
@@ -216,7 +216,7 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
   d.flags = p->flags;
   amr::BuildResult br;
   try {
-    br = amr::build_plan(d, p->tuning.interp_smem_budget);
+    br = amr::build_plan(d, p->tuning.interp_smem_budget, p->tuning.interp_lanes == 32 ? 32 : 32767);
   } catch (const std::bad_alloc&) {
     return AMR_ERR_OUT_OF_MEMORY;
   }
@@ -371,17 +371,18 @@ amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coa
   }
   const int n_reg = p->n_itiles - p->n_cut_itiles;
   const dim3 b(p->tuning.interp_threads);
+  const int L = p->tuning.interp_lanes;
   if (n_reg > 0) {
     const dim3 g(n_reg);
     if (p->precision == AMR_PREC_SPLIT) {
       switch (p->tuning.interp_addback) {
-        case 0: amr::interp_kernel<true, 0><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
-        case 1: amr::interp_kernel<true, 1><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
-        case 3: amr::interp_kernel<true, 3><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
-        default: amr::interp_kernel<true, 2><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr); break;
+        case 0: amr::interp_kernel<true, 0><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr, L); break;
+        case 1: amr::interp_kernel<true, 1><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr, L); break;
+        case 3: amr::interp_kernel<true, 3><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr, L); break;
+        default: amr::interp_kernel<true, 2><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr, L); break;
       }
     } else {
-      amr::interp_kernel<false><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr);
+      amr::interp_kernel<false><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr, L);
     }
     AMR_CUDA(cudaGetLastError());
   }
@@ -389,9 +390,9 @@ amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coa
     const dim3 g(p->n_cut_itiles);
     const amr::Tile* ct = p->itiles_d + n_reg;
     if (p->precision == AMR_PREC_SPLIT)
-      amr::interp_kernel<true, 2, false, true><<<g, b, p->interp_smem, s>>>(p->items_d, ct, p->U, coarse, fine, nullptr, nullptr);
+      amr::interp_kernel<true, 2, false, true><<<g, b, p->interp_smem, s>>>(p->items_d, ct, p->U, coarse, fine, nullptr, nullptr, L);
     else
-      amr::interp_kernel<false, 2, false, true><<<g, b, p->interp_smem, s>>>(p->items_d, ct, p->U, coarse, fine, nullptr, nullptr);
+      amr::interp_kernel<false, 2, false, true><<<g, b, p->interp_smem, s>>>(p->items_d, ct, p->U, coarse, fine, nullptr, nullptr, L);
     AMR_CUDA(cudaGetLastError());
   }
   return AMR_OK;
@@ -405,13 +406,14 @@ amr_status amr_transfer_plan_interpolate_increments(amr_transfer_plan* p, const 
   const int n_reg = p->n_itiles - p->n_cut_itiles;
   if (n_reg > 0) {
     amr::interp_kernel<true, 0, true><<<n_reg, p->tuning.interp_threads, p->interp_smem, (cudaStream_t)stream>>>(
-        p->items_d, p->itiles_d, p->U, coarse, nullptr, increments, p->incr_off_d);
+        p->items_d, p->itiles_d, p->U, coarse, nullptr, increments, p->incr_off_d, p->tuning.interp_lanes);
     AMR_CUDA(cudaGetLastError());
   }
   if (p->n_cut_itiles > 0) {
     amr::interp_kernel<true, 0, true, true><<<p->n_cut_itiles, p->tuning.interp_threads, p->interp_smem,
                                               (cudaStream_t)stream>>>(p->items_d, p->itiles_d + n_reg, p->U, coarse,
-                                                                      nullptr, increments, p->incr_off_d);
+                                                                      nullptr, increments, p->incr_off_d,
+                                                                      p->tuning.interp_lanes);
     AMR_CUDA(cudaGetLastError());
   }
   return AMR_OK;
@@ -489,14 +491,16 @@ amr_status amr_transfer_plan_get_tuning(const amr_transfer_plan* p, amr_transfer
   return AMR_OK;
 }
 
-static bool tuning_valid(const amr_transfer_tuning& t) {
-  auto ok_threads = [](int n) { return n >= 32 && n <= 256 && n % 32 == 0; };
-  return ok_threads(t.interp_threads) && ok_threads(t.restrict_threads) && t.interp_smem_budget >= 4096 &&
-         t.interp_smem_budget <= 196 * 1024 && t.interp_addback >= 0 && t.interp_addback <= 3;
+static bool tuning_valid(const amr_transfer_tuning& t, int precision) {
+  auto ok_threads = [](int n, int max) { return n >= 32 && n <= max && n % 32 == 0; };
+  const int max_interp = precision == AMR_PREC_SPLIT ? amr::kMaxSplitInterpThreads : 256;
+  return ok_threads(t.interp_threads, max_interp) && ok_threads(t.restrict_threads, 256) &&
+         t.interp_smem_budget >= 4096 && t.interp_smem_budget <= 196 * 1024 && t.interp_addback >= 0 &&
+         t.interp_addback <= 3 && (t.interp_lanes == 0 || t.interp_lanes == 32);
 }
 
 amr_status amr_transfer_plan_set_tuning(amr_transfer_plan* p, const amr_transfer_tuning* t) {
-  if (!p || !t || !tuning_valid(*t)) return AMR_ERR_INVALID_ARGUMENT;
+  if (!p || !t || !tuning_valid(*t, p->precision)) return AMR_ERR_INVALID_ARGUMENT;
   drop_graph(p);
   const amr_transfer_tuning old = p->tuning;
   p->tuning = *t;
@@ -518,25 +522,34 @@ amr_status amr_transfer_plan_autotune(amr_transfer_plan* p, const double* coarse
   const int reps = 3;
   amr_transfer_tuning best = p->tuning;
   float best_i = 1e30f, best_r = 1e30f;
-  const int threads[] = {128, 256};
-  const int budgets[] = {24 * 1024, 32 * 1024, 48 * 1024, 64 * 1024, 96 * 1024};
-  for (int th : threads)
-    for (int bud : budgets) {
-      amr_transfer_tuning t = p->tuning;
-      t.interp_threads = th;
-      t.interp_smem_budget = bud;
-      p->tuning = t;
-      if ((st = rebuild_tiles(p)) != AMR_OK) continue;  // e.g. a budget the device cannot hold
-      float ms = 0.f;
-      if ((st = time_runs(s, reps, [&] { return amr_transfer_plan_interpolate(p, coarse, fine, stream); }, &ms)) !=
-          AMR_OK)
-        return st;
-      if (ms < best_i) {
-        best_i = ms;
-        best.interp_threads = th;
-        best.interp_smem_budget = bud;
-      }
+  // (lanes, CTA size, shared-memory budget): dense packing over a range of
+  // budgets; one warp per centre with budgets that fit 32 unknowns of the
+  // common tile regions
+  struct Shape { int lanes, threads, budget; };
+  std::vector<Shape> shapes;
+  for (int th : {128, 256})
+    for (int kb : {24, 32, 48, 64, 96}) shapes.push_back({0, th, kb * 1024});
+  if (p->precision == AMR_PREC_SPLIT)
+    for (int th : {256, amr::kMaxSplitInterpThreads})
+      for (int kb : {64, 112}) shapes.push_back({32, th, kb * 1024});
+  for (const Shape& sh : shapes) {
+    amr_transfer_tuning t = p->tuning;
+    t.interp_lanes = sh.lanes;
+    t.interp_threads = sh.threads;
+    t.interp_smem_budget = sh.budget;
+    p->tuning = t;
+    if ((st = rebuild_tiles(p)) != AMR_OK) continue;  // e.g. a budget the device cannot hold
+    float ms = 0.f;
+    if ((st = time_runs(s, reps, [&] { return amr_transfer_plan_interpolate(p, coarse, fine, stream); }, &ms)) !=
+        AMR_OK)
+      return st;
+    if (ms < best_i) {
+      best_i = ms;
+      best.interp_lanes = sh.lanes;
+      best.interp_threads = sh.threads;
+      best.interp_smem_budget = sh.budget;
     }
+  }
   if (p->precision == AMR_PREC_SPLIT) {
     p->tuning = best;
     if ((st = rebuild_tiles(p)) != AMR_OK) return st;
@@ -553,7 +566,7 @@ amr_status amr_transfer_plan_autotune(amr_transfer_plan* p, const double* coarse
     }
     p->tuning = best;
   }
-  for (int th : threads) {
+  for (int th : {128, 256}) {
     p->tuning.restrict_threads = th;
     float ms = 0.f;
     if ((st = time_runs(s, reps, [&] { return amr_transfer_plan_restrict(p, fine, coarse_out, stream); }, &ms)) !=

@@ -201,7 +201,7 @@ static BuildResult fail(amr_status st, const std::string& msg) {
   return r;
 }
 
-BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
+BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget, int nu_cap) {
   if (desc.abi_version != AMR_TRANSFER_ABI_VERSION)
     return fail(AMR_ERR_INVALID_ARGUMENT, "abi_version mismatch");
   if (desc.num_unknowns < 1) return fail(AMR_ERR_INVALID_ARGUMENT, "num_unknowns must be >= 1");
@@ -279,7 +279,8 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget) {
         IRange rn, ra, rb;
         interp_region(p, k, m, a0, na, b0, nb, rn, ra, rb);
         const int64_t vols = (int64_t)(rn.hi - rn.lo + 1) * (ra.hi - ra.lo + 1) * (rb.hi - rb.lo + 1);
-        const int nu_max = (int)std::min<int64_t>(U, std::max<int64_t>(1, smem_budget / (vols * 8)));
+        const int nu_max =
+            (int)std::min<int64_t>(std::min<int64_t>(U, nu_cap), std::max<int64_t>(1, smem_budget / (vols * 8)));
         const int nchunks = (int)((U + nu_max - 1) / nu_max);
         const int nu = (int)((U + nchunks - 1) / nchunks);
         for (int c = 0; c < nchunks; ++c) {

@@ -100,7 +100,9 @@ struct BuildResult {
   int64_t incr_elems = 0;
 };
 
-BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget);
+// smem_budget: bytes one interpolation tile may stage; nu_cap: the most
+// unknowns one interpolation tile may carry.
+BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget, int nu_cap = 32767);
 
 // Adjoint work: P^T over coarse face arrays (items sharing one coarse array
 // form a group and are summed in item order), R^T over each item's fine

@@ -23,6 +23,10 @@
 
 namespace amr {
 
+// Largest CTA of the split-precision interpolation kernel (two CTAs per SM
+// keep about 80 registers per thread).
+constexpr int kMaxSplitInterpThreads = 384;
+
 __constant__ double c_wt_interp[WT_SIZE];
 __constant__ double c_wt_restrict[WT_SIZE];
 __constant__ float c_wt_interp_f[WT_SIZE];
@@ -348,12 +352,14 @@ struct Counter4 {
 // amr_transfer_plan_interpolate_increments) instead of float64 fine values.
 // CUT: tiles of items whose patch size is not a multiple of 3 (children of
 // one centre may lie in two fine face arrays, see CutAxis).
+// lanes: 0 packs the (centre, unknown) tasks densely, unknown fastest; 32
+// gives each coarse centre one warp, lane = unknown (tiles carry <= 32
+// unknowns), so the per-centre window and weight work is warp-uniform.
 template <bool SPLIT, int ADDBACK = 2, bool INCR = false, bool CUT = false>
-__global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_transfer_item* __restrict__ items,
-                                                     const Tile* __restrict__ tiles, int U,
-                                                     const double* __restrict__ coarse,
-                                                     double* __restrict__ fine, float* __restrict__ incr,
-                                                     const int64_t* __restrict__ incr_off) {
+__global__ void __launch_bounds__(SPLIT ? kMaxSplitInterpThreads : 256, 2)
+    interp_kernel(const amr_transfer_item* __restrict__ items, const Tile* __restrict__ tiles, int U,
+                  const double* __restrict__ coarse, double* __restrict__ fine, float* __restrict__ incr,
+                  const int64_t* __restrict__ incr_off, int lanes) {
   using SType = typename std::conditional<SPLIT, F2, double>::type;
   extern __shared__ double smem_raw[];
   SType* sm = reinterpret_cast<SType*>(smem_raw);
@@ -396,11 +402,17 @@ __global__ void __launch_bounds__(256, SPLIT ? 3 : 2) interp_kernel(const amr_tr
   const int64_t arr = fr.vols * U;
   const float inv_p = 1.0f / (float)p;
   const int SA = nu, SB = NA * nu, SJ = NB * NA * nu;
-  const int ntask = t.na * t.nb * nu;
+  // task walk: (unknown, centre) pairs, or centres only with the lane as the unknown
+  const bool per_warp = lanes == 32;
+  const int lane = threadIdx.x & 31;
+  const int w_nu = per_warp ? 1 : nu;
+  const int e_first = per_warp ? (int)(threadIdx.x >> 5) : (int)threadIdx.x;
+  const int e_step = per_warp ? (int)(blockDim.x >> 5) : (int)blockDim.x;
+  const int ntask = t.na * t.nb * w_nu;
   Counter4 c;
-  c.init(threadIdx.x, blockDim.x, nu, t.na, t.nb);
-  for (int e = threadIdx.x; e < ntask; e += blockDim.x, c.advance(nu, t.na, t.nb)) {
-    const int u = c.u, a = t.a0 + c.x, b = t.b0 + c.y;
+  c.init(e_first, e_step, w_nu, t.na, t.nb);
+  for (int e = (per_warp && lane >= nu) ? ntask : e_first; e < ntask; e += e_step, c.advance(w_nu, t.na, t.nb)) {
+    const int u = per_warp ? lane : c.u, a = t.a0 + c.x, b = t.b0 + c.y;
     ChildMap cm;
     CutAxis ca, cbx;
     if constexpr (CUT) {

@@ -38,15 +38,20 @@ def _check(items, U, c, f, f_gpu, c_gpu, tol):
 
 
 @pytest.mark.parametrize("precision,tol", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6)])
-@pytest.mark.parametrize("shape", [(128, 8192, 128, 0), (256, 24 * 1024, 64, 1), (64, 100 * 1024, 256, 3),
-                                   (256, 64 * 1024, 256, 2)])
+@pytest.mark.parametrize("shape", [(128, 8192, 128, 0, 0), (256, 24 * 1024, 64, 1, 0), (64, 100 * 1024, 256, 3, 0),
+                                   (256, 64 * 1024, 256, 2, 0), (256, 112 * 1024, 128, 2, 32),
+                                   (64, 16 * 1024, 256, 1, 32), (384, 64 * 1024, 256, 3, 32)])
 def test_set_tuning_keeps_parity(shape, precision, tol):
     U = 13
     items, c, f = _batch(U=U)
     plan = B.Plan(items, U, len(c), len(f), precision)
+    if precision == B.PREC_FP64 and shape[0] > 256:  # the float64 kernel's CTA is at most 256 threads
+        with pytest.raises(B.AmrError):
+            plan.set_tuning(*shape)
+        return
     plan.set_tuning(*shape)
     assert plan.tuning == dict(interp_threads=shape[0], interp_smem_budget=shape[1], restrict_threads=shape[2],
-                               interp_addback=shape[3])
+                               interp_addback=shape[3], interp_lanes=shape[4])
     cd, fd = torch.as_tensor(c).cuda(), torch.as_tensor(f).cuda()
     co = cd.clone()
     plan.interpolate(cd, fd)
@@ -57,8 +62,9 @@ def test_set_tuning_keeps_parity(shape, precision, tol):
 
 def test_invalid_tuning_rejected():
     items, c, f = _batch(n=2)
-    plan = B.Plan(items, 13, len(c), len(f))
-    for bad in [(16, 32768, 128), (256, 1024, 128), (256, 32768, 300), (512, 32768, 128), (256, 32768, 128, 4)]:
+    plan = B.Plan(items, 13, len(c), len(f))  # float64: 384 threads is beyond its CTA limit
+    for bad in [(16, 32768, 128), (256, 1024, 128), (256, 32768, 300), (512, 32768, 128), (256, 32768, 128, 4),
+                (256, 32768, 128, 2, 16), (384, 32768, 128, 2, 32)]:
         with pytest.raises(B.AmrError):
             plan.set_tuning(*bad)
 
@@ -88,3 +94,36 @@ def test_launch_without_capture_rejected():
     plan = B.Plan(items, 13, len(c), len(f))
     with pytest.raises(B.AmrError):
         plan.launch_step()
+
+
+@pytest.mark.parametrize("precision", [B.PREC_SPLIT, B.PREC_FP64])
+def test_warp_per_centre_mapping_is_bitwise_identical(precision):
+    """interp_lanes = 32 (one warp per coarse centre, tiles of at most 32
+    unknowns) changes only which thread computes a (centre, unknown) task,
+    so with U = 59 (chunks of 30 and 29) and patch sizes that are and are not
+    multiples of 3 its ghosts equal the dense mapping's bit for bit, and
+    match the oracle."""
+    U = 59
+    rng = np.random.default_rng(23)
+    n = 10
+    ps = [9, 8, 6, 10, 12, 7, 9, 5, 24, 4]
+    items, cl, fl = wl.make_items(rng.integers(0, 6, n), rng.integers(-1, 9, n), ps, rng.choice([2, 3], n),
+                                  rng.choice([1, 2, 3], n), U)
+    g = np.random.Generator(np.random.PCG64(29))
+    coarse, fine = wl.sample_buffers(items, U, cl, fl, wl.SmoothField(U, g), wl.origins_in_box(n, g))
+    cd = coarse.cuda()
+    outs = []
+    threads = 384 if precision == B.PREC_SPLIT else 256
+    for shape in ((256, 64 * 1024, 256, 2, 0), (threads, 112 * 1024, 256, 2, 32), (256, 24 * 1024, 128, 2, 32)):
+        plan = B.Plan(items, U, cl, fl, precision)
+        plan.set_tuning(*shape)
+        fd = fine.cuda().clone()
+        plan.interpolate(cd, fd)
+        torch.cuda.synchronize()
+        outs.append(fd.cpu().numpy())
+        plan.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    c, f = coarse.numpy(), fine.numpy()
+    fm, _ = written_masks(items, U, cl, fl)
+    tol = 1e-12 if precision == B.PREC_FP64 else 2e-6
+    assert normwise_errors(items, U, outs[1], tr.interpolate(items, U, c, f), fm, "fine")[0] <= tol
