@@ -435,15 +435,18 @@ def other_workloads(B, wl, stream):
             it = it9.copy()
             it["order"] = order
             plan = B.Plan(it, 59, c9.numel(), f9.numel(), B.PREC_SPLIT)
+            tuned = plan.autotune(c9, f9, co9)
             info = plan.info
             t = _time_steps(lambda: (plan.interpolate(c9, f9), plan.restrict(f9, co9)), 10, stream)
             row[name] = {"ms_per_step": t,
-                         "value": (info["interp_outputs"] + info["restrict_outputs"]) * 59 / (t * 1e-3)}
+                         "value": (info["interp_outputs"] + info["restrict_outputs"]) * 59 / (t * 1e-3),
+                         "lanes": tuned["interp_lanes"], "threads": tuned["interp_threads"]}
             plan.close()
         sweep[f"p{pp}"] = row
         del it9, c9, f9, co9
     torch.cuda.empty_cache()
-    out["patch_size_sweep"] = {"workload": "k=3, U=59, split precision, ~2,048*81/p^2 hanging faces per p", **sweep}
+    out["patch_size_sweep"] = {"workload": "k=3, U=59, split precision, autotuned, ~2,048*81/p^2 hanging faces per p",
+                               **sweep}
     # uneven batch: 20,000 subface items, p in {6,9,12}, k in {2,3}, orders 1/2/3
     items, coarse, fine = wl.uneven_batch(device="cuda")
     U = 59
