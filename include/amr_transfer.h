@@ -115,9 +115,11 @@ typedef struct amr_transfer_plan amr_transfer_plan; /* opaque, owned by the libr
 amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_plan** out);
 
 /* Q^f = P Q^c (Sec. 2): writes only the fine ghost halves (the k fine layers
- * on the coarse side) of every item's fine face arrays.  coarse and fine are
- * device pointers to coarse_elems / fine_elems float64 values; they must not
- * overlap. */
+ * on the coarse side) of every item's fine face arrays.  coarse and fine
+ * point to coarse_elems / fine_elems float64 values in memory the device can
+ * access: device memory, or pinned host memory, which the kernels then read
+ * and write in place over the host link (same results, bit for bit); they
+ * must not overlap.  The same holds for every buffer of the calls below. */
 amr_status amr_transfer_plan_interpolate(amr_transfer_plan* plan, const double* coarse,
                                          double* fine, void* cuda_stream);
 

@@ -111,12 +111,15 @@ def _items_array(items):
 
 
 def _ptr(x):
-    """Device pointer of a torch tensor (must be contiguous float64 on CUDA) or a raw int."""
+    """Pointer of a contiguous float64 torch tensor in device memory or in
+    pinned host memory (which the kernels read and write in place over the
+    host link), or a raw int."""
     if isinstance(x, int) or x is None:
         return x
     import torch
-    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
-        raise TypeError("buffers must be contiguous float64 CUDA tensors")
+    if not (isinstance(x, torch.Tensor) and (x.is_cuda or x.is_pinned()) and x.dtype == torch.float64
+            and x.is_contiguous()):
+        raise TypeError("buffers must be contiguous float64 tensors on the GPU or in pinned host memory")
     return x.data_ptr()
 
 

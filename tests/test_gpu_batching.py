@@ -127,3 +127,24 @@ def test_warp_per_centre_mapping_is_bitwise_identical(precision):
     fm, _ = written_masks(items, U, cl, fl)
     tol = 1e-12 if precision == B.PREC_FP64 else 2e-6
     assert normwise_errors(items, U, outs[1], tr.interpolate(items, U, c, f), fm, "fine")[0] <= tol
+
+
+def test_pinned_host_buffers_match_device_buffers():
+    """The kernels accept buffers in pinned host memory (read and written in
+    place over the host link): same results, bit for bit, as on device
+    buffers, for interpolate, restrict and a split-precision mixed batch."""
+    U = 13
+    items, c, f = _batch(n=9, U=U, seed=6)
+    plan = B.Plan(items, U, len(c), len(f), B.PREC_SPLIT)
+    cd, fd = torch.as_tensor(c).cuda(), torch.as_tensor(f).cuda()
+    cod = cd.clone()
+    plan.interpolate(cd, fd)
+    plan.restrict(fd, cod)
+    ch, fh = torch.as_tensor(c).pin_memory(), torch.as_tensor(f).pin_memory()
+    coh = ch.clone().pin_memory()
+    plan.interpolate(ch, fh)
+    plan.restrict(fh, coh)
+    torch.cuda.synchronize()
+    assert torch.equal(fd.cpu(), fh) and torch.equal(cod.cpu(), coh)
+    with pytest.raises(TypeError):
+        plan.interpolate(torch.as_tensor(c), fh)  # pageable host memory is refused by the binding
