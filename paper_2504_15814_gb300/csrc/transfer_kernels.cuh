@@ -109,61 +109,68 @@ __device__ __forceinline__ void taylor_interp_core(const Diff& D, const Emit& em
       if (d == 2) C[0][0][r] = acc[r];
     }
   }
-  // mixed derivatives over the planes (d, e): 3x3 windows
+  // Mixed derivatives.  Every axis's mixed window has 3 points (ms[d] ..
+  // ms[d] + 2) for Taylor orders, so all of them come from one 3x3x3 box of
+  // values, collapsed axis by axis: along the normal into (value at c, r = 1,
+  // r = 2) -- the normal window is centred on layer -1, as 2k >= m + 1 >= 3 --
+  // then along t0 into (value at c, r = 1, r = 2) with c's box index sa, then
+  // along t1 likewise.  Each box value is read once.
+  {
+    const T* wn = W(3, c[0] - ms[0], 1);  // rows r = 1, 2 at +0, +3
+    const T* wa = W(3, c[1] - ms[1], 1);
+    const T* wb = W(3, c[2] - ms[2], 1);
+    const int sa = c[1] - ms[1], sb = c[2] - ms[2];
+    T m110 = T(0), m011 = T(0), m101 = T(0);                          // second order
+    T m210 = T(0), m120 = T(0), m201 = T(0), m102 = T(0), m021 = T(0), m012 = T(0), m111 = T(0);  // third
 #pragma unroll
-  for (int d = 0; d < 3; ++d)
+    for (int q = 0; q < 3; ++q) {  // t1 index in the box
+      T p11 = T(0), p10 = T(0), p01 = T(0), p21 = T(0), p12 = T(0), p20 = T(0), p02 = T(0);
 #pragma unroll
-    for (int e = d + 1; e < 3; ++e) {
-      const T* wd = W(ml[d], c[d] - ms[d], 1);  // rows r = 1, 2 follow at +3, +6
-      const T* we = W(ml[e], c[e] - ms[e], 1);
-      T acc11 = T(0), acc21 = T(0), acc12 = T(0);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        // first collapse along d for this e-line
-        T s1 = T(0), s2 = T(0);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          int x[3] = {c[0], c[1], c[2]};
-          x[d] = ms[d] + i;
-          x[e] = ms[e] + q;
-          const T v = D(x[0], x[1], x[2]);
-          s1 += wd[i] * v;
-          if (M == 3) s2 += wd[3 + i] * v;
-        }
-        acc11 += we[q] * s1;
+      for (int j = 0; j < 3; ++j) {  // t0 index in the box
+        const T x0 = D(ms[0], ms[1] + j, ms[2] + q);
+        const T x1 = D(ms[0] + 1, ms[1] + j, ms[2] + q);
+        const T x2 = D(ms[0] + 2, ms[1] + j, ms[2] + q);
+        const T s1 = wn[0] * x0 + wn[1] * x1 + wn[2] * x2;  // d/dn
+        const T a1 = wa[j], ea = j == sa ? T(1) : T(0);
+        p11 += a1 * s1;
+        p10 += ea * s1;
+        p01 += a1 * x1;  // x1: the normal point at c
         if (M == 3) {
-          acc21 += we[q] * s2;
-          acc12 += we[3 + q] * s1;
+          const T s2 = wn[3] * x0 + wn[4] * x1 + wn[5] * x2;  // d2/dn2
+          const T a2 = wa[3 + j];
+          p21 += a1 * s2;
+          p12 += a2 * s1;
+          p20 += ea * s2;
+          p02 += a2 * x1;
         }
       }
-      int r3[3] = {0, 0, 0};
-      r3[d] = 1; r3[e] = 1;
-      C[r3[0]][r3[1]][r3[2]] = acc11;
+      const T b1 = wb[q], eb = q == sb ? T(1) : T(0);
+      m110 += eb * p11;
+      m101 += b1 * p10;
+      m011 += b1 * p01;
       if (M == 3) {
-        r3[d] = 2; r3[e] = 1;
-        C[r3[0]][r3[1]][r3[2]] = acc21;
-        r3[d] = 1; r3[e] = 2;
-        C[r3[0]][r3[1]][r3[2]] = acc12;
+        const T b2 = wb[3 + q];
+        m210 += eb * p21;
+        m120 += eb * p12;
+        m201 += b1 * p20;
+        m102 += b2 * p10;
+        m021 += b1 * p02;
+        m012 += b2 * p01;
+        m111 += b1 * p11;
       }
     }
-  if (M == 3) {  // u_{n t0 t1} on the 3x3x3 box
-    const T* w0 = W(ml[0], c[0] - ms[0], 1);
-    const T* w1 = W(ml[1], c[1] - ms[1], 1);
-    const T* w2 = W(ml[2], c[2] - ms[2], 1);
-    T acc = T(0);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      T sq = T(0);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        T sj = T(0);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) sj += w0[i] * D(ms[0] + i, ms[1] + j, ms[2] + q);
-        sq += w1[j] * sj;
-      }
-      acc += w2[q] * sq;
+    C[1][1][0] = m110;
+    C[1][0][1] = m101;
+    C[0][1][1] = m011;
+    if (M == 3) {
+      C[2][1][0] = m210;
+      C[1][2][0] = m120;
+      C[2][0][1] = m201;
+      C[1][0][2] = m102;
+      C[0][2][1] = m021;
+      C[0][1][2] = m012;
+      C[1][1][1] = m111;
     }
-    C[1][1][1] = acc;
   }
 
   // Evaluate at the children with even/odd splitting, axis by axis.

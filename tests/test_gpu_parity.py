@@ -138,12 +138,15 @@ def test_overlapping_buffers_rejected():
 
 def test_full_size_uniform_batch_sampled():
     """2,048 hanging faces, p = 9, k = 3, U = 59, Taylor-3 (the benchmark
-    workload, same launch): 3,000 sampled outputs of each operator against
-    the oracle, one by one."""
+    workload, in the launch shape the benchmark times: autotuned on these
+    buffers, as bench.py does): 3,000 sampled outputs of each operator
+    against the oracle, one by one."""
     items, coarse, fine = wl.uniform_batch(device="cuda")
     U = 59
     for precision, tol in ((B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND)):
         plan = B.Plan(items, U, coarse.numel(), fine.numel(), precision)
+        tuned = plan.autotune(coarse, fine.clone(), coarse.clone())
+        record(test="full_size_sampled_tuning", precision=precision, **tuned)
         f_out = fine.clone()
         plan.interpolate(coarse, f_out)
         c_out = coarse.clone()
