@@ -411,11 +411,14 @@ def other_workloads(B, wl, stream):
     items, coarse, fine = wl.uniform_batch(n_faces=2048, U=59, order=3, config_index=1, device="cuda")
     co = coarse.clone()
     rows = {}
-    for name, scheme, flags in (("least_squares", 1, 0), ("csr_finite_difference", 0, B.FLAG_CSR)):
+    for name, scheme, flags in (("least_squares", 1, 0), ("least_squares_csr", 1, B.FLAG_CSR),
+                                ("csr_finite_difference", 0, B.FLAG_CSR)):
         it = items.copy()
         it["scheme"] = scheme
         for prec_name, prec in (("split", B.PREC_SPLIT), ("fp64", B.PREC_FP64)):
             plan = B.Plan(it, 59, coarse.numel(), fine.numel(), prec, flags)
+            if not flags:
+                plan.autotune(coarse, fine, co)
             info = plan.info
             t = _time_steps(lambda: (plan.interpolate(coarse, fine), plan.restrict(fine, co)), 5, stream)
             rows[f"{name}_{prec_name}"] = {"ms_per_step": t,

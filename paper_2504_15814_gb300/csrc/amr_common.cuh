@@ -159,8 +159,27 @@ __host__ __device__ inline int ls_index(int k, int j, int i) { return ((k - 1) *
 // Combined Taylor restriction weights: coarse halo layer j >= 1 of a face with
 // overlap k (2 or 3) and order m (2 or 3) is sum_i W[i] u(fine layer s + i)
 // over the derivative window (s, L) about fine layer k - 1 (Sec. 3: Taylor
-// about the nearest fine cell, extrapolated by (3j + 2 - k) h).
-constexpr int RW_SIZE = 8 * 5;
-__host__ __device__ inline int rw_index(int order, int k, int j) { return (((order - 2) * 2 + (k - 2)) * 2 + (j - 1)) * 5; }
+// about the nearest fine cell, extrapolated by (3j + 2 - k) h), for the
+// finite-difference (scheme 0) or least-squares (scheme 1) derivatives.
+constexpr int RW_SIZE = 16 * 5;
+__host__ __device__ inline int rw_index(int order, int k, int j, int scheme = 0) {
+  return ((((scheme * 2 + order - 2) * 2 + (k - 2)) * 2) + (j - 1)) * 5;
+}
+
+// Least-squares interpolation (scheme 1) in the factorised kernel: the
+// derivatives of a coarse centre are W^T d over the values d of the
+// finite-difference stencils' slots -- the three pure lines (slot 5 d + i,
+// point ps[d] + i along axis d, i < the window length) and the 3x3x3 box of
+// the mixed windows (slot 15 + (q * 3 + j) * 3 + i, point (ms0 + i, ms1 + j,
+// ms2 + q)).  W depends on where the centre sits along each tangential axis
+// (ls_class: first, second, interior, second-last, last), so a table block
+// per (p, k, order) holds LS_CLASSES slot x derivative matrices, then the
+// per-class column sums of W.
+constexpr int LS_SLOTS = 42;
+constexpr int LS_NALPHA = 19;  // derivatives 0 < |alpha| <= 3
+constexpr int LS_CLASSES = 25;
+constexpr int LS_BLOCK = LS_CLASSES * (LS_SLOTS + 1) * LS_NALPHA;
+__host__ __device__ inline int ls_class(int a, int p) { return a < 2 ? a : (a > p - 3 ? 4 - (p - 1 - a) : 2); }
+__host__ __device__ inline int ls_class_rep(int cls, int p) { return cls < 3 ? cls : p - 5 + cls; }
 
 }  // namespace amr

@@ -104,7 +104,11 @@ struct amr_transfer_plan {
   amr::Tile* itiles_d = nullptr;
   amr::Tile* rtiles_d = nullptr;
   int n_itiles = 0, n_rtiles = 0;
-  int n_cut_itiles = 0;  // the last n_cut_itiles interpolation tiles run the CUT kernel variant
+  int n_iseg[4] = {0, 0, 0, 0};  // interpolation tile segments: FD, FD + CUT, least squares, least squares + CUT
+  // least-squares derivative tables (items with scheme 1)
+  float* ls_wf_d = nullptr;
+  double* ls_wd_d = nullptr;
+  int64_t* ls_off_d = nullptr;
   // forward sparse rows of the items routed to the CSR kernels
   int n_cpt = 0, n_crt = 0;
   amr::CsrTile *cpt_d = nullptr, *crt_d = nullptr;
@@ -143,6 +147,8 @@ static void free_plan(amr_transfer_plan* p) {
   void* csr[] = {p->cpt_d, p->crt_d, p->pf_row_d, p->rf_row_d, p->pf_col_d, p->rf_col_d, p->pf_out_d,
                  p->rf_out_d, p->pf_base_d, p->rf_base_d, p->pf_val_d, p->rf_val_d, p->pf_valf_d};
   for (void* q : csr) cudaFree(q);
+  void* ls[] = {p->ls_wf_d, p->ls_wd_d, p->ls_off_d};
+  for (void* q : ls) cudaFree(q);
   void* ptrs[] = {p->items_d, p->itiles_d, p->rtiles_d, p->incr_off_d, p->incr_tiles_d, p->pt_tiles_d, p->rt_tiles_d, p->group_ptr_d,
                   p->group_items_d, p->item_class_d, p->cls_pt_rows_d, p->cls_rt_rows_d, p->pt_row_ptr_d,
                   p->rt_row_ptr_d, p->pt_col_d, p->rt_col_d, p->pt_val_d, p->rt_val_d};
@@ -200,7 +206,9 @@ const char* amr_last_cuda_error(void) { return g_cuda_error.c_str(); }
 
 // Kernel launches of one interpolate call.
 static int interp_launch_count(const amr_transfer_plan* p) {
-  return (p->n_itiles - p->n_cut_itiles > 0 ? 1 : 0) + (p->n_cut_itiles > 0 ? 1 : 0) + (p->n_cpt > 0 ? 1 : 0);
+  int n = p->n_cpt > 0 ? 1 : 0;
+  for (int q = 0; q < 4; ++q) n += p->n_iseg[q] > 0 ? 1 : 0;
+  return n;
 }
 
 // (Re)build the forward tiles of a plan for its tuning (synchronous).
@@ -239,14 +247,18 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
     return st;
   }
   if (br.max_interp_smem > 48 * 1024) {
-    const void* fns[9] = {(const void*)amr::interp_kernel<false>, (const void*)amr::interp_kernel<true, 0>,
-                          (const void*)amr::interp_kernel<true, 1>, (const void*)amr::interp_kernel<true, 2>,
-                          (const void*)amr::interp_kernel<true, 3>, (const void*)amr::interp_kernel<true, 0, true>,
-                          (const void*)amr::interp_kernel<false, 2, false, true>,
-                          (const void*)amr::interp_kernel<true, 2, false, true>,
-                          (const void*)amr::interp_kernel<true, 0, true, true>};
+    const void* fns[] = {(const void*)amr::interp_kernel<false>, (const void*)amr::interp_kernel<true, 0>,
+                         (const void*)amr::interp_kernel<true, 1>, (const void*)amr::interp_kernel<true, 2>,
+                         (const void*)amr::interp_kernel<true, 3>, (const void*)amr::interp_kernel<true, 0, true>,
+                         (const void*)amr::interp_kernel<false, 2, false, true>,
+                         (const void*)amr::interp_kernel<true, 2, false, true>,
+                         (const void*)amr::interp_kernel<true, 0, true, true>,
+                         (const void*)amr::interp_kernel<false, 2, false, false, true>,
+                         (const void*)amr::interp_kernel<false, 2, false, true, true>,
+                         (const void*)amr::interp_kernel<true, 2, false, false, true>,
+                         (const void*)amr::interp_kernel<true, 2, false, true, true>};
     cudaError_t e = cudaSuccess;
-    for (int q = 0; q < 9 && e == cudaSuccess; ++q)
+    for (size_t q = 0; q < sizeof fns / sizeof fns[0] && e == cudaSuccess; ++q)
       e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, br.max_interp_smem);
     if (e != cudaSuccess) {
       cudaFree(it);
@@ -267,7 +279,7 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
   p->n_incr_tiles = (int)br.incr_tiles.size();
   p->info.increment_elems = br.incr_elems;
   p->n_itiles = (int)br.interp_tiles.size();
-  p->n_cut_itiles = (int)br.n_cut_interp_tiles;
+  for (int q = 0; q < 4; ++q) p->n_iseg[q] = (int)br.interp_segments[q];
   p->n_rtiles = (int)br.restrict_tiles.size();
   p->interp_smem = br.max_interp_smem;
   p->info.num_items = d.num_items;
@@ -306,6 +318,22 @@ static amr_status build_csr_tables(amr_transfer_plan* p, const amr_transfer_desc
   return AMR_OK;
 }
 
+// Upload the least-squares derivative tables of the scheme-1 items (plan create).
+static amr_status upload_ls_tables(amr_transfer_plan* p, const amr_transfer_desc& d) {
+  amr::LsTables lt;
+  try {
+    lt = amr::build_ls_tables(d);
+  } catch (const std::bad_alloc&) {
+    return AMR_ERR_OUT_OF_MEMORY;
+  }
+  if (lt.wd.empty()) return AMR_OK;
+  amr_status st;
+  if ((st = upload(lt.wd, &p->ls_wd_d)) != AMR_OK || (st = upload(lt.wf, &p->ls_wf_d)) != AMR_OK ||
+      (st = upload(lt.item_off, &p->ls_off_d)) != AMR_OK)
+    return st;
+  return AMR_OK;
+}
+
 amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_plan** out) {
   if (!out) return AMR_ERR_INVALID_ARGUMENT;
   *out = nullptr;
@@ -334,7 +362,7 @@ amr_status amr_transfer_plan_create(const amr_transfer_desc* desc, amr_transfer_
   p->items_h.assign(desc->items, desc->items + desc->num_items);
   p->flags = desc->flags;
   if ((st = upload(p->items_h, &p->items_d)) != AMR_OK || (st = rebuild_tiles(p)) != AMR_OK ||
-      (st = build_csr_tables(p, *desc)) != AMR_OK) {
+      (st = build_csr_tables(p, *desc)) != AMR_OK || (st = upload_ls_tables(p, *desc)) != AMR_OK) {
     free_plan(p);
     return st;
   }
@@ -369,30 +397,42 @@ amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coa
                                                                  p->U, coarse, fine);
     AMR_CUDA(cudaGetLastError());
   }
-  const int n_reg = p->n_itiles - p->n_cut_itiles;
   const dim3 b(p->tuning.interp_threads);
   const int L = p->tuning.interp_lanes;
-  if (n_reg > 0) {
-    const dim3 g(n_reg);
-    if (p->precision == AMR_PREC_SPLIT) {
+  const amr::Tile* seg = p->itiles_d;
+  const bool split = p->precision == AMR_PREC_SPLIT;
+  for (int q = 0; q < 4; seg += p->n_iseg[q], ++q) {
+    if (p->n_iseg[q] == 0) continue;
+    const dim3 g(p->n_iseg[q]);
+    const int z = p->interp_smem;
+    const amr_transfer_item* it = p->items_d;
+    const int U = p->U;
+    if (q == 0 && split) {
       switch (p->tuning.interp_addback) {
-        case 0: amr::interp_kernel<true, 0><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr, L); break;
-        case 1: amr::interp_kernel<true, 1><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr, L); break;
-        case 3: amr::interp_kernel<true, 3><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr, L); break;
-        default: amr::interp_kernel<true, 2><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr, L); break;
+        case 0: amr::interp_kernel<true, 0><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L); break;
+        case 1: amr::interp_kernel<true, 1><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L); break;
+        case 3: amr::interp_kernel<true, 3><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L); break;
+        default: amr::interp_kernel<true, 2><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L); break;
       }
+    } else if (q == 0) {
+      amr::interp_kernel<false><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L);
+    } else if (q == 1 && split) {
+      amr::interp_kernel<true, 2, false, true><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L);
+    } else if (q == 1) {
+      amr::interp_kernel<false, 2, false, true><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L);
+    } else if (q == 2 && split) {
+      amr::interp_kernel<true, 2, false, false, true><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L,
+                                                                       p->ls_wf_d, p->ls_wd_d, p->ls_off_d);
+    } else if (q == 2) {
+      amr::interp_kernel<false, 2, false, false, true><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L,
+                                                                        p->ls_wf_d, p->ls_wd_d, p->ls_off_d);
+    } else if (split) {
+      amr::interp_kernel<true, 2, false, true, true><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L,
+                                                                      p->ls_wf_d, p->ls_wd_d, p->ls_off_d);
     } else {
-      amr::interp_kernel<false><<<g, b, p->interp_smem, s>>>(p->items_d, p->itiles_d, p->U, coarse, fine, nullptr, nullptr, L);
+      amr::interp_kernel<false, 2, false, true, true><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L,
+                                                                       p->ls_wf_d, p->ls_wd_d, p->ls_off_d);
     }
-    AMR_CUDA(cudaGetLastError());
-  }
-  if (p->n_cut_itiles > 0) {
-    const dim3 g(p->n_cut_itiles);
-    const amr::Tile* ct = p->itiles_d + n_reg;
-    if (p->precision == AMR_PREC_SPLIT)
-      amr::interp_kernel<true, 2, false, true><<<g, b, p->interp_smem, s>>>(p->items_d, ct, p->U, coarse, fine, nullptr, nullptr, L);
-    else
-      amr::interp_kernel<false, 2, false, true><<<g, b, p->interp_smem, s>>>(p->items_d, ct, p->U, coarse, fine, nullptr, nullptr, L);
     AMR_CUDA(cudaGetLastError());
   }
   return AMR_OK;
@@ -403,16 +443,16 @@ amr_status amr_transfer_plan_interpolate_increments(amr_transfer_plan* p, const 
   amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, increments, p ? p->info.increment_elems / 2 : 0);
   if (st != AMR_OK) return st;
   if (p->n_cpt > 0 || p->n_crt > 0) return AMR_ERR_UNSUPPORTED;  // increments come from the factorised kernel
-  const int n_reg = p->n_itiles - p->n_cut_itiles;
-  if (n_reg > 0) {
-    amr::interp_kernel<true, 0, true><<<n_reg, p->tuning.interp_threads, p->interp_smem, (cudaStream_t)stream>>>(
+  if (p->n_iseg[2] > 0 || p->n_iseg[3] > 0) return AMR_ERR_UNSUPPORTED;  // finite-difference items only
+  if (p->n_iseg[0] > 0) {
+    amr::interp_kernel<true, 0, true><<<p->n_iseg[0], p->tuning.interp_threads, p->interp_smem, (cudaStream_t)stream>>>(
         p->items_d, p->itiles_d, p->U, coarse, nullptr, increments, p->incr_off_d, p->tuning.interp_lanes);
     AMR_CUDA(cudaGetLastError());
   }
-  if (p->n_cut_itiles > 0) {
-    amr::interp_kernel<true, 0, true, true><<<p->n_cut_itiles, p->tuning.interp_threads, p->interp_smem,
-                                              (cudaStream_t)stream>>>(p->items_d, p->itiles_d + n_reg, p->U, coarse,
-                                                                      nullptr, increments, p->incr_off_d,
+  if (p->n_iseg[1] > 0) {
+    amr::interp_kernel<true, 0, true, true><<<p->n_iseg[1], p->tuning.interp_threads, p->interp_smem,
+                                              (cudaStream_t)stream>>>(p->items_d, p->itiles_d + p->n_iseg[0], p->U,
+                                                                      coarse, nullptr, increments, p->incr_off_d,
                                                                       p->tuning.interp_lanes);
     AMR_CUDA(cudaGetLastError());
   }

@@ -55,6 +55,9 @@ Q lagrange_taylor_coeff(int L, int pos, int r, int i) {
   return poly[r] / denom;
 }
 
+std::vector<double> ls_taylor_weights(const std::vector<std::array<int, 3>>& rel, int order,
+                                      const std::array<long double, 3>& off);
+
 Tables make_tables() {
   Tables t{};
   for (int L = 3; L <= 5; ++L)
@@ -116,6 +119,22 @@ Tables make_tables() {
           t.rw[idx] = w.to_double();
           t.rw_hi[idx] = (float)t.rw[idx];
           t.rw_lo[idx] = (float)(t.rw[idx] - (double)t.rw_hi[idx]);
+        }
+        // least-squares scheme: the fit along the same window through the
+        // expansion value (the base takes 1 - sum of the others)
+        std::vector<std::array<int, 3>> rel;
+        for (int i = 0; i < L; ++i)
+          if (i != pos) rel.push_back({i - pos, 0, 0});
+        const std::vector<double> wl = ls_taylor_weights(rel, order, {(long double)e, 0.0L, 0.0L});
+        double sum = 0.0;
+        for (size_t q = 0; q < rel.size(); ++q) sum += wl[q];
+        for (int i = 0; i < 5; ++i) {
+          double w = 0.0;
+          if (i < L) w = i == pos ? 1.0 - sum : wl[i < pos ? i : i - 1];
+          const int idx = rw_index(order, k, j, 1) + i;
+          t.rw[idx] = w;
+          t.rw_hi[idx] = (float)w;
+          t.rw_lo[idx] = (float)(w - (double)t.rw_hi[idx]);
         }
       }
   return t;
@@ -267,12 +286,13 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget, int nu_ca
 
   // Tiles and byte counts.
   const int TMAX = 12;
-  // interpolation tiles of items whose patch size is not a multiple of 3
-  // (children of one coarse centre may lie in two fine face arrays) go to a
-  // second list, appended after the others and run by their own kernel variant
-  std::vector<Tile> cut_tiles;
+  // interpolation tiles go to one of four segments, each run by its own
+  // kernel variant: patch size a multiple of 3 or not (children of one
+  // coarse centre may lie in two fine face arrays), finite-difference or
+  // least-squares derivatives
+  std::vector<Tile> seg[4];
   auto add_interp_tiles = [&](int64_t it, int sub, int slot, int alo, int ahi, int blo, int bhi, int p, int k, int m) {
-    std::vector<Tile>& dst = p % 3 ? cut_tiles : r.interp_tiles;
+    std::vector<Tile>& dst = seg[(p % 3 ? 1 : 0) + (desc.items[it].scheme == 1 ? 2 : 0)];
     for (int a0 = alo; a0 < ahi; a0 += TMAX)
       for (int b0 = blo; b0 < bhi; b0 += TMAX) {
         const int na = std::min(TMAX, ahi - a0), nb = std::min(TMAX, bhi - b0);
@@ -353,8 +373,10 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget, int nu_ca
   }
   r.interp_bytes += r.interp_outputs * U * 8;
   r.restrict_bytes += r.restrict_outputs * U * 8;
-  r.n_cut_interp_tiles = (int64_t)cut_tiles.size();
-  r.interp_tiles.insert(r.interp_tiles.end(), cut_tiles.begin(), cut_tiles.end());
+  for (int q = 0; q < 4; ++q) {
+    r.interp_segments[q] = (int64_t)seg[q].size();
+    r.interp_tiles.insert(r.interp_tiles.end(), seg[q].begin(), seg[q].end());
+  }
   return r;
 }
 
@@ -422,32 +444,48 @@ std::vector<std::pair<int, double>> dlin_axis(int c, int n, int e) {
 // Taylor's formula at offset `off`; returns the weight of each point (the
 // centre gets 1 - sum).  Derivatives the points carry no information about
 // (zero columns) are not fitted; their terms vanish at `off` by construction.
-std::vector<double> ls_taylor_weights(const std::vector<std::array<int, 3>>& rel, int order,
-                                      const std::array<long double, 3>& off) {
+// The derivatives 0 < |alpha| <= order in the order the kernels use.
+std::vector<std::array<int, 3>> taylor_alphas(int order) {
   std::vector<std::array<int, 3>> alphas;
   for (int x = 0; x <= order; ++x)
     for (int y = 0; x + y <= order; ++y)
       for (int z = 0; x + y + z <= order; ++z)
         if (x + y + z > 0) alphas.push_back({x, y, z});
-  auto fact = [](int n) { long double f = 1; for (int q = 2; q <= n; ++q) f *= q; return f; };
+  return alphas;
+}
+
+long double factorial(int n) {
+  long double f = 1;
+  for (int q = 2; q <= n; ++q) f *= q;
+  return f;
+}
+
+// Least-squares fit of the derivatives D^alpha u (unit spacing,
+// taylor_alphas order) of the Taylor polynomial through u(c) to the
+// differences d_q = u(c + r_q) - u(c) at the points rel: returns coef[a][q]
+// with D^alpha u = sum_q coef[a][q] d_q, by the normal equations in long
+// double.  Derivatives the points carry no
+// information about (zero columns) are not fitted: their rows are zero.
+std::vector<std::vector<long double>> ls_fit(const std::vector<std::array<int, 3>>& rel, int order) {
+  const std::vector<std::array<int, 3>> alphas = taylor_alphas(order);
   auto basis = [&](const std::array<int, 3>& r, const std::array<int, 3>& a) {
     long double v = 1;
-    for (int d = 0; d < 3; ++d) v *= std::pow((long double)r[d], a[d]) / fact(a[d]);
+    for (int d = 0; d < 3; ++d) v *= std::pow((long double)r[d], a[d]) / factorial(a[d]);
     return v;
   };
-  std::vector<std::array<int, 3>> used;
-  for (auto& a : alphas) {
+  std::vector<int> used;
+  for (size_t a = 0; a < alphas.size(); ++a) {
     bool any = false;
-    for (auto& r : rel) any |= basis(r, a) != 0;
-    if (any) used.push_back(a);
+    for (auto& r : rel) any |= basis(r, alphas[a]) != 0;
+    if (any) used.push_back((int)a);
   }
   const int n = (int)used.size(), m = (int)rel.size();
   // augmented normal equations [A^T A | A^T]
   std::vector<std::vector<long double>> aug(n, std::vector<long double>(n + m, 0));
   for (int i = 0; i < n; ++i) {
     for (int j = 0; j < n; ++j)
-      for (int q = 0; q < m; ++q) aug[i][j] += basis(rel[q], used[i]) * basis(rel[q], used[j]);
-    for (int q = 0; q < m; ++q) aug[i][n + q] = basis(rel[q], used[i]);
+      for (int q = 0; q < m; ++q) aug[i][j] += basis(rel[q], alphas[used[i]]) * basis(rel[q], alphas[used[j]]);
+    for (int q = 0; q < m; ++q) aug[i][n + q] = basis(rel[q], alphas[used[i]]);
   }
   for (int col = 0; col < n; ++col) {
     int piv = col;
@@ -462,12 +500,24 @@ std::vector<double> ls_taylor_weights(const std::vector<std::array<int, 3>>& rel
         for (int c = 0; c < n + m; ++c) aug[r][c] -= f * aug[col][c];
       }
   }
-  std::vector<double> w(m, 0.0);
-  for (int i = 0; i < n; ++i) {
-    long double coeff = 1;
-    for (int d = 0; d < 3; ++d) coeff *= std::pow(off[d], used[i][d]) / fact(used[i][d]);
-    if (coeff == 0) continue;
-    for (int q = 0; q < m; ++q) w[q] += (double)(coeff * aug[i][n + q]);
+  std::vector<std::vector<long double>> coef(alphas.size(), std::vector<long double>(m, 0));
+  for (int i = 0; i < n; ++i)
+    for (int q = 0; q < m; ++q) coef[used[i]][q] = aug[i][n + q];
+  return coef;
+}
+
+// Weights of the least-squares Taylor-m reconstruction at offset `off` on the
+// points rel (the centre gets 1 - sum).
+std::vector<double> ls_taylor_weights(const std::vector<std::array<int, 3>>& rel, int order,
+                                      const std::array<long double, 3>& off) {
+  const std::vector<std::array<int, 3>> alphas = taylor_alphas(order);
+  const std::vector<std::vector<long double>> coef = ls_fit(rel, order);
+  std::vector<double> w(rel.size(), 0.0);
+  for (size_t a = 0; a < alphas.size(); ++a) {
+    long double mono = 1;
+    for (int d = 0; d < 3; ++d) mono *= std::pow(off[d], alphas[a][d]) / factorial(alphas[a][d]);
+    if (mono == 0) continue;
+    for (size_t q = 0; q < rel.size(); ++q) w[q] += (double)(mono * coef[a][q]);
   }
   return w;
 }
@@ -572,25 +622,13 @@ Rows restriction_rows(int sub, int slot, int p, int k, int order, int scheme) {
           }
         } else if (j == 0) {
           row[pack_vol(slot, 1 + k, q1, q0)] = 1.0;
-        } else if (scheme == 1) {
-          int s, L;
-          stencil_window(k - 1, -k, k - 1, pure_exactness(order), s, L);
-          std::vector<std::array<int, 3>> rel;
-          for (int i = s; i < s + L; ++i)
-            if (i != k - 1) rel.push_back({i - (k - 1), 0, 0});
-          const std::array<long double, 3> off{(long double)(3 * j + 2 - k), 0.0L, 0.0L};
-          const std::vector<double> w = ls_taylor_weights(rel, order, off);
-          double sum = 0.0;
-          for (size_t q = 0; q < rel.size(); ++q) {
-            row[pack_vol(slot, k - 1 + rel[q][0] + k, q1, q0)] += w[q];
-            sum += w[q];
-          }
-          row[pack_vol(slot, k - 1 + k, q1, q0)] += 1.0 - sum;
         } else {
+          // combined weights of the window about fine layer k - 1 (finite
+          // differences, or the least-squares fit along the same window)
           int s, L;
           stencil_window(k - 1, -k, k - 1, pure_exactness(order), s, L);
           for (int i = 0; i < L; ++i) {
-            const double wv = t.rw[rw_index(order, k, j) + i];
+            const double wv = t.rw[rw_index(order, k, j, scheme) + i];
             if (wv != 0.0) row[pack_vol(slot, s + i + k, q1, q0)] += wv;
           }
         }
@@ -679,8 +717,82 @@ AdjointBuild build_adjoint(const amr_transfer_desc& desc) {
 // ---------------------------------------------------------------------------
 namespace amr {
 
-bool csr_routed(const amr_transfer_desc& desc, const amr_transfer_item& x) {
-  return x.scheme == 1 || (desc.flags & AMR_FLAG_CSR) != 0;
+bool csr_routed(const amr_transfer_desc& desc, const amr_transfer_item&) {
+  return (desc.flags & AMR_FLAG_CSR) != 0;
+}
+
+LsTables build_ls_tables(const amr_transfer_desc& desc) {
+  LsTables lt;
+  std::map<std::tuple<int, int, int>, int64_t> blocks;
+  for (int64_t it = 0; it < desc.num_items; ++it) {
+    const amr_transfer_item& x = desc.items[it];
+    if (x.scheme != 1 || csr_routed(desc, x)) {
+      lt.item_off.push_back(-1);
+      continue;
+    }
+    const int p = x.patch_size, k = x.overlap, order = x.order;
+    auto key = std::make_tuple(p, k, order);
+    auto f = blocks.find(key);
+    if (f == blocks.end()) {
+      const int64_t off = (int64_t)lt.wd.size();
+      lt.wd.resize(off + LS_BLOCK, 0.0);
+      double* W = lt.wd.data() + off;
+      double* sums = W + LS_CLASSES * LS_SLOTS * LS_NALPHA;
+      const std::vector<std::array<int, 3>> alphas = taylor_alphas(order);
+      for (int cls = 0; cls < LS_CLASSES; ++cls) {
+        const int a = ls_class_rep(cls % 5, p), b = ls_class_rep(cls / 5, p);
+        if (a < 0 || a >= p || b < 0 || b >= p) continue;
+        const int c[3] = {-1, a, b}, lo[3] = {-k, 0, 0}, hi[3] = {k - 1, p - 1, p - 1};
+        int ps[3], pl[3], ms[3], ml[3];
+        for (int d = 0; d < 3; ++d) {
+          stencil_window(c[d], lo[d], hi[d], pure_exactness(order), ps[d], pl[d]);
+          stencil_window(c[d], lo[d], hi[d], mixed_exactness(order), ms[d], ml[d]);
+        }
+        // the kernel's slots and their points
+        std::vector<std::pair<int, std::array<int, 3>>> slots;
+        for (int d = 0; d < 3; ++d)
+          for (int i = 0; i < pl[d]; ++i) {
+            std::array<int, 3> xq{c[0], c[1], c[2]};
+            xq[d] = ps[d] + i;
+            slots.push_back({d * 5 + i, xq});
+          }
+        for (int q = 0; q < 3; ++q)
+          for (int j = 0; j < 3; ++j)
+            for (int i = 0; i < 3; ++i)
+              slots.push_back({15 + (q * 3 + j) * 3 + i, {ms[0] + i, ms[1] + j, ms[2] + q}});
+        // each support point (but the centre) on its first slot
+        std::set<std::array<int, 3>> support;
+        for (auto& xq : stencil_support(c, lo, hi, order))
+          if (xq[0] != c[0] || xq[1] != c[1] || xq[2] != c[2]) support.insert(xq);
+        std::vector<int> slot_of;
+        std::vector<std::array<int, 3>> rel;
+        std::set<std::array<int, 3>> done;
+        for (auto& [sl, xq] : slots)
+          if (support.count(xq) && !done.count(xq)) {
+            done.insert(xq);
+            slot_of.push_back(sl);
+            rel.push_back({xq[0] - c[0], xq[1] - c[1], xq[2] - c[2]});
+          }
+        if (done.size() != support.size()) std::abort();  // the slots cover the support by construction
+        const std::vector<std::vector<long double>> coef = ls_fit(rel, order);
+        for (size_t al = 0; al < alphas.size(); ++al) {
+          long double scale = 1;
+          for (int d = 0; d < 3; ++d) scale *= factorial(alphas[al][d]) * std::pow(3.0L, alphas[al][d]);
+          long double sum = 0;
+          for (size_t q = 0; q < rel.size(); ++q) {
+            const long double w = coef[al][q] / scale;
+            W[(cls * LS_SLOTS + slot_of[q]) * LS_NALPHA + al] = (double)w;
+            sum += w;
+          }
+          sums[cls * LS_NALPHA + al] = (double)sum;
+        }
+      }
+      f = blocks.emplace(key, off).first;
+    }
+    lt.item_off.push_back(f->second);
+  }
+  lt.wf.assign(lt.wd.begin(), lt.wd.end());
+  return lt;
 }
 
 CsrBuild build_csr(const amr_transfer_desc& desc) {

@@ -80,6 +80,18 @@ struct CsrBuild {
 };
 CsrBuild build_csr(const amr_transfer_desc& desc);
 
+// Least-squares derivative tables of the scheme-1 items that the factorised
+// interpolation kernel serves: one block of LS_BLOCK weights per distinct
+// (p, k, order), layout [class][slot][alpha] then [class][alpha] (column
+// sums); alpha / (alpha! 3^|alpha|) scaling folded in (Taylor coefficients in
+// units of the fine spacing, like the finite-difference tables).
+struct LsTables {
+  std::vector<double> wd;
+  std::vector<float> wf;
+  std::vector<int64_t> item_off;  // per item: offset of its block, or -1
+};
+LsTables build_ls_tables(const amr_transfer_desc& desc);
+
 struct AdjointTile {
   int32_t index;  // group (P^T) or item (R^T)
   int16_t slot;   // fine face array within the item (R^T)
@@ -91,7 +103,10 @@ struct BuildResult {
   amr_status status = AMR_OK;
   std::string message;
   std::vector<Tile> interp_tiles, restrict_tiles;
-  int64_t n_cut_interp_tiles = 0;  // the last ones of interp_tiles: items with p not a multiple of 3
+  // interp_tiles holds four consecutive segments, counted here: finite
+  // differences, then with p not a multiple of 3 (CUT), then least squares,
+  // then least squares with CUT
+  int64_t interp_segments[4] = {0, 0, 0, 0};
   int64_t interp_outputs = 0, restrict_outputs = 0;
   int64_t interp_bytes = 0, restrict_bytes = 0;
   int max_interp_smem = 0;  // bytes of dynamic shared memory the interpolation kernel needs

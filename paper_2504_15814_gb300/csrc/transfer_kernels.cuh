@@ -54,6 +54,62 @@ template <> struct Arith<true> {
 template <typename T>
 struct Tri { T m, z, p; };
 
+// Evaluate the Taylor polynomial with coefficients C (units of the fine
+// spacing) at the children of a coarse centre, by even/odd splitting, axis by
+// axis; emit(ii, e0, e1, v) as for taylor_interp_core.
+template <int M, typename T, typename Emit>
+__device__ __forceinline__ void taylor_children(const T (&C)[M + 1][M + 1][M + 1], const Emit& emit, int k) {
+  // Step A (normal): R[y][z] at e_n in {-1, 0, +1}.
+  Tri<T> R[M + 1][M + 1];
+#pragma unroll
+  for (int y = 0; y <= M; ++y)
+#pragma unroll
+    for (int z = 0; y + z <= M; ++z) {
+      T ev = T(0), od = T(0);
+#pragma unroll
+      for (int x = 2; x + y + z <= M; x += 2) ev += C[x][y][z];
+#pragma unroll
+      for (int x = 1; x + y + z <= M; x += 2) od += C[x][y][z];
+      const T c0 = C[0][y][z];
+      R[y][z].z = c0;
+      R[y][z].p = (c0 + ev) + od;
+      R[y][z].m = (c0 + ev) - od;
+    }
+#pragma unroll
+  for (int ii = 0; ii < 3; ++ii) {
+    if (ii >= k) break;
+    auto pick = [&](const Tri<T>& t) -> T { return ii == 0 ? t.p : (ii == 1 ? t.z : t.m); };
+    Tri<T> Sg[M + 1];  // Step B (t0) for this normal offset
+#pragma unroll
+    for (int z = 0; z <= M; ++z) {
+      T ev = T(0), od = T(0);
+#pragma unroll
+      for (int y = 2; y + z <= M; y += 2) ev += pick(R[y][z]);
+#pragma unroll
+      for (int y = 1; y + z <= M; y += 2) od += pick(R[y][z]);
+      const T c0 = pick(R[0][z]);
+      Sg[z].z = c0;
+      Sg[z].p = (c0 + ev) + od;
+      Sg[z].m = (c0 + ev) - od;
+    }
+#pragma unroll
+    for (int e0 = -1; e0 <= 1; ++e0) {  // Step C (t1)
+      T q[M + 1];
+#pragma unroll
+      for (int z = 0; z <= M; ++z) q[z] = e0 < 0 ? Sg[z].m : (e0 == 0 ? Sg[z].z : Sg[z].p);
+      T ev = T(0), od = T(0);
+#pragma unroll
+      for (int z = 2; z <= M; z += 2) ev += q[z];
+#pragma unroll
+      for (int z = 1; z <= M; z += 2) od += q[z];
+      emit(ii, e0, -1, (q[0] + ev) - od);
+      emit(ii, e0, 0, q[0]);
+      emit(ii, e0, 1, (q[0] + ev) + od);
+    }
+  }
+}
+
+
 // ---------------------------------------------------------------------------
 // Taylor-m interpolation of one coarse centre (layer -1, a, b) and one
 // unknown.  D(j, a', b') returns the input value (float64 path) or its
@@ -131,27 +187,29 @@ __device__ __forceinline__ void taylor_interp_core(const Diff& D, const Emit& em
         const T x1 = D(ms[0] + 1, ms[1] + j, ms[2] + q);
         const T x2 = D(ms[0] + 2, ms[1] + j, ms[2] + q);
         const T s1 = wn[0] * x0 + wn[1] * x1 + wn[2] * x2;  // d/dn
-        const T a1 = wa[j], ea = j == sa ? T(1) : T(0);
+        const T a1 = wa[j];
         p11 += a1 * s1;
-        p10 += ea * s1;
         p01 += a1 * x1;  // x1: the normal point at c
+        if (j == sa) p10 = s1;  // point evaluation at c along t0: a select, no arithmetic
         if (M == 3) {
           const T s2 = wn[3] * x0 + wn[4] * x1 + wn[5] * x2;  // d2/dn2
           const T a2 = wa[3 + j];
           p21 += a1 * s2;
           p12 += a2 * s1;
-          p20 += ea * s2;
           p02 += a2 * x1;
+          if (j == sa) p20 = s2;
         }
       }
-      const T b1 = wb[q], eb = q == sb ? T(1) : T(0);
-      m110 += eb * p11;
+      const T b1 = wb[q];
+      if (q == sb) m110 = p11;  // point evaluation at c along t1
       m101 += b1 * p10;
       m011 += b1 * p01;
       if (M == 3) {
         const T b2 = wb[3 + q];
-        m210 += eb * p21;
-        m120 += eb * p12;
+        if (q == sb) {
+          m210 = p21;
+          m120 = p12;
+        }
         m201 += b1 * p20;
         m102 += b2 * p10;
         m021 += b1 * p02;
@@ -173,55 +231,76 @@ __device__ __forceinline__ void taylor_interp_core(const Diff& D, const Emit& em
     }
   }
 
-  // Evaluate at the children with even/odd splitting, axis by axis.
-  // Step A (normal): R[y][z] at e_n in {-1, 0, +1}.
-  Tri<T> R[M + 1][M + 1];
+  taylor_children<M, T>(C, emit, k);
+}
+
+// Least-squares Taylor-m interpolation of one coarse centre (scheme 1; the
+// paper's fit of all derivatives at once, Sec. 3): the derivatives are
+// W^T d over the slots of the finite-difference stencils (the pure lines and
+// the 3x3x3 box of the mixed windows, slot layout in amr_common.cuh), W the
+// host's fit for the centre's class.  D, emit and c000 as for
+// taylor_interp_core; with RAW (float64 path) D returns input values rather
+// than differences, so c000 times the column sums of W is subtracted.
+template <int M, bool RAW, typename T, typename Diff, typename Emit>
+__device__ __forceinline__ void ls_interp_core(const Diff& D, const Emit& emit, const T* __restrict__ wcls,
+                                               const T* __restrict__ wsum, int k, int p, int a, int b, T c000) {
+  constexpr int NA = M == 3 ? 19 : 9;
+  const int c[3] = {-1, a, b};
+  const int lo[3] = {-k, 0, 0};
+  const int hi[3] = {k - 1, p - 1, p - 1};
+  int ps[3], pl[3], ms[3], ml[3];
 #pragma unroll
-  for (int y = 0; y <= M; ++y)
-#pragma unroll
-    for (int z = 0; y + z <= M; ++z) {
-      T ev = T(0), od = T(0);
-#pragma unroll
-      for (int x = 2; x + y + z <= M; x += 2) ev += C[x][y][z];
-#pragma unroll
-      for (int x = 1; x + y + z <= M; x += 2) od += C[x][y][z];
-      const T c0 = C[0][y][z];
-      R[y][z].z = c0;
-      R[y][z].p = (c0 + ev) + od;
-      R[y][z].m = (c0 + ev) - od;
-    }
-#pragma unroll
-  for (int ii = 0; ii < 3; ++ii) {
-    if (ii >= k) break;
-    auto pick = [&](const Tri<T>& t) -> T { return ii == 0 ? t.p : (ii == 1 ? t.z : t.m); };
-    Tri<T> Sg[M + 1];  // Step B (t0) for this normal offset
-#pragma unroll
-    for (int z = 0; z <= M; ++z) {
-      T ev = T(0), od = T(0);
-#pragma unroll
-      for (int y = 2; y + z <= M; y += 2) ev += pick(R[y][z]);
-#pragma unroll
-      for (int y = 1; y + z <= M; y += 2) od += pick(R[y][z]);
-      const T c0 = pick(R[0][z]);
-      Sg[z].z = c0;
-      Sg[z].p = (c0 + ev) + od;
-      Sg[z].m = (c0 + ev) - od;
-    }
-#pragma unroll
-    for (int e0 = -1; e0 <= 1; ++e0) {  // Step C (t1)
-      T q[M + 1];
-#pragma unroll
-      for (int z = 0; z <= M; ++z) q[z] = e0 < 0 ? Sg[z].m : (e0 == 0 ? Sg[z].z : Sg[z].p);
-      T ev = T(0), od = T(0);
-#pragma unroll
-      for (int z = 2; z <= M; z += 2) ev += q[z];
-#pragma unroll
-      for (int z = 1; z <= M; z += 2) od += q[z];
-      emit(ii, e0, -1, (q[0] + ev) - od);
-      emit(ii, e0, 0, q[0]);
-      emit(ii, e0, 1, (q[0] + ev) + od);
-    }
+  for (int d = 0; d < 3; ++d) {
+    stencil_window(c[d], lo[d], hi[d], pure_exactness(M), ps[d], pl[d]);
+    stencil_window(c[d], lo[d], hi[d], mixed_exactness(M), ms[d], ml[d]);
   }
+  T acc[NA];
+#pragma unroll
+  for (int al = 0; al < NA; ++al) acc[al] = T(0);
+  auto add = [&](int slot, T v) {
+#pragma unroll
+    for (int al = 0; al < NA; ++al) acc[al] += __ldg(wcls + slot * LS_NALPHA + al) * v;
+  };
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      if (i < pl[d]) {
+        int x[3] = {c[0], c[1], c[2]};
+        x[d] = ps[d] + i;
+        add(d * 5 + i, D(x[0], x[1], x[2]));
+      }
+  const int sa = c[1] - ms[1], sb = c[2] - ms[2];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        // Taylor-2 uses only the three planes through the centre (the normal
+        // window is centred on layer -1: i == 1)
+        if (M == 3 || i == 1 || j == sa || q == sb) add(15 + (q * 3 + j) * 3 + i, D(ms[0] + i, ms[1] + j, ms[2] + q));
+  if (RAW) {
+#pragma unroll
+    for (int al = 0; al < NA; ++al) acc[al] -= __ldg(wsum + al) * c000;
+  }
+  T C[M + 1][M + 1][M + 1];
+#pragma unroll
+  for (int x = 0; x <= M; ++x)
+#pragma unroll
+    for (int y = 0; y <= M; ++y)
+#pragma unroll
+      for (int z = 0; z <= M; ++z) C[x][y][z] = T(0);
+  C[0][0][0] = c000;
+  int al = 0;  // the host's derivative order: x, then y, then z ascending
+#pragma unroll
+  for (int x = 0; x <= M; ++x)
+#pragma unroll
+    for (int y = 0; x + y <= M; ++y)
+#pragma unroll
+      for (int z = 0; x + y + z <= M; ++z)
+        if (x + y + z > 0) C[x][y][z] = acc[al++];
+  taylor_children<M, T>(C, emit, k);
 }
 
 // 1-D d-linear child values at offsets -1, 0, +1 from neighbours xm, x0, xp
@@ -362,11 +441,14 @@ struct Counter4 {
 // lanes: 0 packs the (centre, unknown) tasks densely, unknown fastest; 32
 // gives each coarse centre one warp, lane = unknown (tiles carry <= 32
 // unknowns), so the per-centre window and weight work is warp-uniform.
-template <bool SPLIT, int ADDBACK = 2, bool INCR = false, bool CUT = false>
+// LS: least-squares derivatives (scheme 1) from the tables ls_wf / ls_wd at
+// the item's block ls_off[item].
+template <bool SPLIT, int ADDBACK = 2, bool INCR = false, bool CUT = false, bool LS = false>
 __global__ void __launch_bounds__(SPLIT ? kMaxSplitInterpThreads : 256, 2)
     interp_kernel(const amr_transfer_item* __restrict__ items, const Tile* __restrict__ tiles, int U,
                   const double* __restrict__ coarse, double* __restrict__ fine, float* __restrict__ incr,
-                  const int64_t* __restrict__ incr_off, int lanes) {
+                  const int64_t* __restrict__ incr_off, int lanes, const float* __restrict__ ls_wf = nullptr,
+                  const double* __restrict__ ls_wd = nullptr, const int64_t* __restrict__ ls_off = nullptr) {
   using SType = typename std::conditional<SPLIT, F2, double>::type;
   extern __shared__ double smem_raw[];
   SType* sm = reinterpret_cast<SType*>(smem_raw);
@@ -484,14 +566,32 @@ __global__ void __launch_bounds__(SPLIT ? kMaxSplitInterpThreads : 256, 2)
         else v = add_back(hc, incr);
         store(ii, e0, e1, v);
       };
-      if (m == 3) taylor_interp_core<3, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
-      else if (m == 2) taylor_interp_core<2, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
-      else dlinear_interp_core<float>(D, emit, k, p, a, b);
+      if constexpr (LS) {
+        const int cls = ls_class(a, p) + 5 * ls_class(b, p);
+        const float* wb = ls_wf + ls_off[t.item];
+        const float* wc = wb + cls * LS_SLOTS * LS_NALPHA;
+        const float* ws = wb + LS_CLASSES * LS_SLOTS * LS_NALPHA + cls * LS_NALPHA;
+        if (m == 3) ls_interp_core<3, false, float>(D, emit, wc, ws, k, p, a, b, 0.f);
+        else ls_interp_core<2, false, float>(D, emit, wc, ws, k, p, a, b, 0.f);
+      } else {
+        if (m == 3) taylor_interp_core<3, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
+        else if (m == 2) taylor_interp_core<2, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
+        else dlinear_interp_core<float>(D, emit, k, p, a, b);
+      }
     } else {
       auto emit = [&](int ii, int e0, int e1, double v) { store(ii, e0, e1, v); };
-      if (m == 3) taylor_interp_core<3, double>(S, emit, c_wt_interp, k, p, a, b, S(-1, a, b));
-      else if (m == 2) taylor_interp_core<2, double>(S, emit, c_wt_interp, k, p, a, b, S(-1, a, b));
-      else dlinear_interp_core<double>(S, emit, k, p, a, b);
+      if constexpr (LS) {
+        const int cls = ls_class(a, p) + 5 * ls_class(b, p);
+        const double* wb = ls_wd + ls_off[t.item];
+        const double* wc = wb + cls * LS_SLOTS * LS_NALPHA;
+        const double* ws = wb + LS_CLASSES * LS_SLOTS * LS_NALPHA + cls * LS_NALPHA;
+        if (m == 3) ls_interp_core<3, true, double>(S, emit, wc, ws, k, p, a, b, S(-1, a, b));
+        else ls_interp_core<2, true, double>(S, emit, wc, ws, k, p, a, b, S(-1, a, b));
+      } else {
+        if (m == 3) taylor_interp_core<3, double>(S, emit, c_wt_interp, k, p, a, b, S(-1, a, b));
+        else if (m == 2) taylor_interp_core<2, double>(S, emit, c_wt_interp, k, p, a, b, S(-1, a, b));
+        else dlinear_interp_core<double>(S, emit, k, p, a, b);
+      }
     }
   }
 }
@@ -556,7 +656,7 @@ __device__ __forceinline__ double pick5(const double* v, int idx) {
 // weighted sum; each output rebuilt as float64 without float64 instructions.
 template <typename Store>
 __device__ __forceinline__ void taylor_extrapolate_split(const double* v, int L, int pos, int m, int k, int j0,
-                                                         const Store& store) {
+                                                         int scheme, const Store& store) {
   const F2 b = split_f64(pick5(v, pos));
   float dh[5], dl[5];
 #pragma unroll
@@ -571,7 +671,7 @@ __device__ __forceinline__ void taylor_extrapolate_split(const double* v, int L,
     }
   }
   for (int j = j0; j < k; ++j) {
-    const int w0 = rw_index(m, k, j);
+    const int w0 = rw_index(m, k, j, scheme);
     float ah = 0.f, al = 0.f;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
@@ -716,15 +816,15 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
           // layer 1 with float64 combined weights (the float64 unit is idle
           // here), deeper layers with float-pair arithmetic: the two pipes
           // share the work
-          const double* w = c_rw + rw_index(m, k, 1);
+          const double* w = c_rw + rw_index(m, k, 1, it.scheme);
           double acc = 0.0;
 #pragma unroll
           for (int i = 0; i < 5; ++i) acc = fma(w[i], v[r][i], acc);
           col[gs_n] = acc;
-          if (k > 2) taylor_extrapolate_split(v[r], L, pos, m, k, 2, [&](int j, double out) { col[j * gs_n] = out; });
+          if (k > 2) taylor_extrapolate_split(v[r], L, pos, m, k, 2, it.scheme, [&](int j, double out) { col[j * gs_n] = out; });
         } else {
           for (int j = 1; j < k; ++j) {
-            const double* w = c_rw + rw_index(m, k, j);
+            const double* w = c_rw + rw_index(m, k, j, it.scheme);
             double acc = 0.0;
 #pragma unroll
             for (int i = 0; i < 5; ++i) acc = fma(w[i], v[r][i], acc);

@@ -102,7 +102,6 @@ def test_adjoints_match_oracle_transposes(order):
     for s in range(9):  # nine subfaces sharing one coarse face array
         items[s] = (1, s, p, k, order, 0, 0, s * arr)
     for j, (f, pp) in enumerate(((0, 4), (3, 8), (5, 5))):
-        a = 2 * k * pp * pp * U
         items[9 + j] = (f, -1, pp, k, order, 0, arr + j * 2 * 8 * 8 * k * U, 9 * arr + j * 9 * 2 * 8 * 8 * k * U)
     cl, fl = arr + 3 * 2 * 8 * 8 * k * U, 9 * arr + 3 * 9 * 2 * 8 * 8 * k * U
     rng = np.random.default_rng(order)
@@ -121,9 +120,10 @@ def test_adjoints_match_oracle_transposes(order):
 
 
 @pytest.mark.parametrize("scheme,flags", [(1, 0), (0, B.FLAG_CSR)])
-def test_sparse_row_kernels(scheme, flags):
-    """The least-squares scheme and AMR_FLAG_CSR run through the sparse-row
-    kernels, whose rows the host builds for any patch size."""
+def test_least_squares_and_sparse_row_kernels(scheme, flags):
+    """The least-squares scheme (factorised kernels, CUT variant for these
+    patch sizes) and AMR_FLAG_CSR (sparse-row kernels, whose rows the host
+    builds for any patch size)."""
     n = 8
     orders = [3, 2, 3, 2, 3, 2, 3, 2] if scheme else [1, 2, 3, 1, 2, 3, 1, 2]
     items, c, f = _batch(list(range(6)) + [2, 5], [-1, 4, -1, 0, 8, -1, 3, -1], [4, 5, 7, 8, 10, 5, 7, 4],

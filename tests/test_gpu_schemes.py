@@ -1,6 +1,7 @@
 """GPU parity of the least-squares scheme (paper Sec. 3 read as a
-least-squares polynomial fit) and of the sparse-row (CSR) kernels that also
-serve every item under AMR_FLAG_CSR, against the oracle."""
+least-squares polynomial fit; the factorised kernels with per-class fit
+tables) and of the sparse-row (CSR) kernels that serve every item under
+AMR_FLAG_CSR, against the oracle."""
 import numpy as np
 import pytest
 import torch
@@ -41,11 +42,17 @@ def _check(items, U, c, f, precision, tol_i, tol_r, flags=0, tag=""):
     return plan
 
 
-@pytest.mark.parametrize("precision,tol_i", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6)])
+# Split-precision restriction: injection, one float64 layer and float-pair
+# deeper layers, so its error stays near 2^-44 of sum |w_i| |u_i - u_base|.
+SPLIT_RESTRICT_TOL = 1e-10
+
+
+@pytest.mark.parametrize("precision,tol_i,tol_r", [(B.PREC_FP64, 1e-12, 1e-12),
+                                                   (B.PREC_SPLIT, 2e-6, SPLIT_RESTRICT_TOL)])
 @pytest.mark.parametrize("order", [2, 3])
-def test_least_squares_items(order, precision, tol_i):
+def test_least_squares_items(order, precision, tol_i, tol_r):
     items, c, f = _batch([order] * 12, [1] * 12)
-    _check(items, 7, c, f, precision, tol_i, 1e-12, tag=f"ls{order}")
+    _check(items, 7, c, f, precision, tol_i, tol_r, tag=f"ls{order}")
 
 
 def test_mixed_fd_and_ls_items_in_one_plan():
@@ -81,9 +88,28 @@ def test_least_squares_adjoint_matches_oracle_transposes():
     assert rel(of.cpu().numpy(), ref_f) <= 1e-12
 
 
-def test_increments_rejected_on_sparse_row_plans():
-    items, c, f = _batch([3] * 3, [1] * 3)
-    plan = B.Plan(items, 7, len(c), len(f), B.PREC_SPLIT)
+@pytest.mark.parametrize("scheme,flags", [(1, 0), (0, B.FLAG_CSR)])
+def test_increments_rejected_on_least_squares_and_sparse_row_plans(scheme, flags):
+    items, c, f = _batch([3] * 3, [scheme] * 3)
+    plan = B.Plan(items, 7, len(c), len(f), B.PREC_SPLIT, flags)
     incr = torch.empty(plan.info["increment_elems"], dtype=torch.float32, device="cuda")
     with pytest.raises(B.AmrError):
         plan.interpolate_increments(torch.as_tensor(c).cuda(), incr)
+
+
+@pytest.mark.parametrize("precision,tol_i", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6)])
+def test_least_squares_factorised_equals_sparse_rows(precision, tol_i):
+    """The same least-squares operators through the factorised kernels and
+    through the sparse-row kernels (AMR_FLAG_CSR), with the one-warp-per-
+    centre mapping on the factorised side."""
+    items, c, f = _batch([3, 2, 3, 3, 2, 3], [1] * 6, U=31, seed=13)
+    a = B.Plan(items, 31, len(c), len(f), precision)
+    if precision == B.PREC_SPLIT:
+        a.set_tuning(384, 112 * 1024, 256, 2, 32)
+    b = B.Plan(items, 31, len(c), len(f), precision, B.FLAG_CSR)
+    fa, fb = gpu_interpolate(a, c, f), gpu_interpolate(b, c, f)
+    fm, cm = written_masks(items, 31, len(c), len(f))
+    assert normwise_errors(items, 31, fa, fb, fm, "fine")[0] <= tol_i
+    ca, cb = gpu_restrict(a, f, c), gpu_restrict(b, f, c)
+    tol_r = 1e-12 if precision == B.PREC_FP64 else SPLIT_RESTRICT_TOL
+    assert normwise_errors(items, 31, ca, cb, cm, "coarse")[0] <= tol_r
