@@ -1,0 +1,81 @@
+"""Host logic of the CUDA path, on the CPU: the explicit operator rows the
+builder derives (used by the sparse-row kernels and the adjoints), its
+least-squares class tables as the interpolation kernel applies them, and
+its restriction rows, compared with the oracle's rows for the finite-
+difference and least-squares schemes, patch sizes that are and are not
+multiples of 3.  A small harness (tests/host/builder_rows.cpp) is compiled
+against the builder sources with the CUDA toolkit's nvcc."""
+import collections
+import os
+import shutil
+import subprocess
+
+import pytest
+
+from oracle import operators as op
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path_factory.mktemp("host") / "builder_rows")
+    cmd = [nvcc, "-std=c++17", "-O1", "-o", exe, os.path.join(HERE, "host", "builder_rows.cpp"),
+           os.path.join(ROOT, "paper_2504_15814_gb300", "csrc", "builder.cpp")]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return exe
+
+
+def _rows(exe, *args):
+    out = subprocess.run([exe, *map(str, args)], check=True, capture_output=True, text=True).stdout
+    rows = collections.defaultdict(dict)
+    for line in out.splitlines():
+        o, c, w = line.split()
+        rows[int(o)][int(c)] = rows[int(o)].get(int(c), 0.0) + float(w)
+    return rows
+
+
+def _worst(got, outs, rows):
+    assert set(got) <= set(outs)
+    worst = 0.0
+    for o, row in zip(outs, rows):
+        g = got.get(o, {})
+        scale = max(1.0, max(abs(w) for w in row.values()))
+        worst = max(worst, max(abs(g.get(c, 0.0) - row.get(c, 0.0)) for c in set(g) | set(row)) / scale)
+    return worst
+
+
+CASES = [(9, 3, 3, 4), (9, 3, 2, 0), (6, 2, 3, 8), (8, 3, 3, 2), (5, 2, 2, 4), (4, 3, 3, 6), (12, 2, 3, 1)]
+
+
+DLINEAR = [(9, 3, 1, 4), (7, 2, 1, 3), (5, 1, 1, 0)]
+
+
+@pytest.mark.parametrize("p,k,order,sub", CASES + DLINEAR)
+@pytest.mark.parametrize("scheme", [op.SCHEME_FD, op.SCHEME_LS])
+def test_interpolation_rows_match_oracle(harness, p, k, order, sub, scheme):
+    if order == 1 and scheme == op.SCHEME_LS:
+        pytest.skip("least squares needs a Taylor order")
+    outs, rows = op.interpolation_rows(0, sub, p, k, order, scheme=scheme)
+    assert _worst(_rows(harness, "interp", p, k, order, sub, scheme), outs, rows) < 1e-13
+
+
+@pytest.mark.parametrize("p,k,order,sub", CASES + DLINEAR)
+@pytest.mark.parametrize("scheme", [op.SCHEME_FD, op.SCHEME_LS])
+def test_restriction_rows_match_oracle(harness, p, k, order, sub, scheme):
+    if order == 1 and scheme == op.SCHEME_LS:
+        pytest.skip("least squares needs a Taylor order")
+    outs, rows = op.restriction_rows(0, sub, p, k, order, scheme=scheme)
+    assert _worst(_rows(harness, "restrict", p, k, order, sub, scheme), outs, rows) < 1e-13
+
+
+@pytest.mark.parametrize("p,k,order,sub", CASES)
+def test_least_squares_class_tables_match_oracle(harness, p, k, order, sub):
+    """The per-class fit tables, applied over the kernel's stencil slots,
+    give the oracle's least-squares interpolation rows."""
+    outs, rows = op.interpolation_rows(0, sub, p, k, order, scheme=op.SCHEME_LS)
+    assert _worst(_rows(harness, "lsclass", p, k, order, sub), outs, rows) < 1e-13
