@@ -143,14 +143,19 @@ class Plan:
         h = ctypes.c_void_p()
         _check(lib().amr_transfer_plan_create(ctypes.byref(desc), ctypes.byref(h)), "amr_transfer_plan_create")
         self._handle = h
+        import torch
+        self.device = torch.cuda.current_device()  # the plan's tables live on this device
         self.num_unknowns = int(num_unknowns)
         self.coarse_elems = int(coarse_elems)
         self.fine_elems = int(fine_elems)
         self.precision = int(precision)
 
     def _sized(self, x, n, name):
-        if not isinstance(x, int) and x is not None and x.numel() < n:
-            raise ValueError(f"{name} holds {x.numel()} elements, the plan needs {n}")
+        if not isinstance(x, int) and x is not None:
+            if x.numel() < n:
+                raise ValueError(f"{name} holds {x.numel()} elements, the plan needs {n}")
+            if x.is_cuda and x.device.index != self.device:
+                raise ValueError(f"{name} is on cuda:{x.device.index}, the plan on cuda:{self.device}")
         return _ptr(x)
 
     def interpolate(self, coarse, fine, stream=None):

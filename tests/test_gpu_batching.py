@@ -26,15 +26,23 @@ def _batch(n=9, U=13, seed=1):
 
 
 def _check(items, U, c, f, f_gpu, c_gpu, tol):
-    """Each operator against the oracle on the same inputs: interpolation on
-    the original data, restriction on the fine buffer the GPU step produced
-    (restriction reads the interpolated ghost layers, and Taylor
-    extrapolation would amplify their split-precision error)."""
+    """Each operator against the oracle on the same original inputs:
+    f_gpu = P applied to (c, f), c_gpu = R applied to (f, c)."""
     f_ref = tr.interpolate(items, U, c, f)
-    c_ref = tr.restrict(items, U, f_gpu, c)
+    c_ref = tr.restrict(items, U, f, c)
     fm, cm = written_masks(items, U, len(c), len(f))
     assert normwise_errors(items, U, f_gpu, f_ref, fm, "fine")[0] <= tol
     assert normwise_errors(items, U, c_gpu, c_ref, cm, "coarse")[0] <= tol
+
+
+def _operators(plan, c, f):
+    """Interpolation of (c, f) and restriction of the original (f, c) on the GPU."""
+    cd, fd = torch.as_tensor(c).cuda(), torch.as_tensor(f).cuda()
+    co = cd.clone()
+    plan.interpolate(cd, fd)
+    plan.restrict(torch.as_tensor(f).cuda(), co)
+    torch.cuda.synchronize()
+    return fd.cpu().numpy(), co.cpu().numpy()
 
 
 @pytest.mark.parametrize("precision,tol", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6)])
@@ -52,12 +60,7 @@ def test_set_tuning_keeps_parity(shape, precision, tol):
     plan.set_tuning(*shape)
     assert plan.tuning == dict(interp_threads=shape[0], interp_smem_budget=shape[1], restrict_threads=shape[2],
                                interp_addback=shape[3], interp_lanes=shape[4])
-    cd, fd = torch.as_tensor(c).cuda(), torch.as_tensor(f).cuda()
-    co = cd.clone()
-    plan.interpolate(cd, fd)
-    plan.restrict(fd, co)
-    torch.cuda.synchronize()
-    _check(items, U, c, f, fd.cpu().numpy(), co.cpu().numpy(), tol)
+    _check(items, U, c, f, *_operators(plan, c, f), tol)
 
 
 def test_invalid_tuning_rejected():
@@ -79,14 +82,21 @@ def test_autotune_and_step_graph(precision, tol):
     co = cd.clone()
     chosen = plan.autotune(cd, fd, co)
     assert chosen == plan.tuning
-    # the step graph replays interpolate + restrict on the captured buffers
+    # the chosen shape keeps parity with the oracle
+    _check(items, U, c, f, *_operators(plan, c, f), tol)
+    # the step graph replays interpolate + restrict on the captured buffers:
+    # the same results, bit for bit, as the two calls made directly
     fd.copy_(torch.as_tensor(f))
     co.copy_(cd)
     plan.capture_step(cd, fd, co)
     for _ in range(2):
         plan.launch_step()
+    f2, c2 = torch.as_tensor(f).cuda(), cd.clone()
+    for _ in range(2):
+        plan.interpolate(cd, f2)
+        plan.restrict(f2, c2)
     torch.cuda.synchronize()
-    _check(items, U, c, f, fd.cpu().numpy(), co.cpu().numpy(), tol)
+    assert torch.equal(fd, f2) and torch.equal(co, c2)
 
 
 def test_launch_without_capture_rejected():
