@@ -814,14 +814,24 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
         col[0] = pick5(v[r], 1 - s);  // layer 0 coincides with fine layer 1
         if (SPLIT) {
           // layer 1 with float64 combined weights (the float64 unit is idle
-          // here), deeper layers with float-pair arithmetic: the two pipes
-          // share the work
+          // here); layer 2 in float64 for the first column of the pair and in
+          // float-pair arithmetic for the second: the two pipes share the work
           const double* w = c_rw + rw_index(m, k, 1, it.scheme);
           double acc = 0.0;
 #pragma unroll
           for (int i = 0; i < 5; ++i) acc = fma(w[i], v[r][i], acc);
           col[gs_n] = acc;
-          if (k > 2) taylor_extrapolate_split(v[r], L, pos, m, k, 2, it.scheme, [&](int j, double out) { col[j * gs_n] = out; });
+          if (k > 2) {
+            if (r == 0) {
+              const double* w2 = c_rw + rw_index(m, k, 2, it.scheme);
+              double acc2 = 0.0;
+#pragma unroll
+              for (int i = 0; i < 5; ++i) acc2 = fma(w2[i], v[r][i], acc2);
+              col[2 * gs_n] = acc2;
+            } else {
+              taylor_extrapolate_split(v[r], L, pos, m, k, 2, it.scheme, [&](int j, double out) { col[j * gs_n] = out; });
+            }
+          }
         } else {
           for (int j = 1; j < k; ++j) {
             const double* w = c_rw + rw_index(m, k, j, it.scheme);
