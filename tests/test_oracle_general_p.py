@@ -8,7 +8,9 @@ Checked against facts that do not reuse the oracle's formulas: exact
 reproduction of polynomials of the scheme's degree at centres placed by the
 workload generator, the ownership partition (every fine-side coarse volume
 restricted exactly once, at a coincident fine centre), a hand-derived d-linear
-row on a cut volume, and the convergence order on a smooth field."""
+row on a cut volume, and the convergence order on a smooth field.  Also
+pinned here: overlaps k > 3 (deeper ghost layers), which the oracle's
+geometry covers although the GPU path stops at k = 3."""
 import math
 from fractions import Fraction as F
 
@@ -141,3 +143,25 @@ def test_convergence_order_p8(order, expected):
     for errs in (errs_i, errs_r):
         rates = [math.log2(errs[j] / errs[j + 1]) for j in range(len(errs) - 1)]
         assert abs(rates[-1] - expected) < 0.3, rates
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("k", [4, 5])
+def test_deeper_overlaps_reproduce_polynomials(k, order):
+    """Overlaps beyond the paper's 3 (fine ghost layers then have nearest
+    coarse centres in deeper coarse layers; restriction injects every coarse
+    layer whose centre coincides with a fine one): exact on polynomials of
+    the scheme's degree (linear for d-linear)."""
+    rng = np.random.default_rng(50 * k + order)
+    p = 9
+    for face, sub in ((0, 4), (4, 0), (2, 8)):
+        cpos, fpos = _positions(face, sub, p, k)
+        q = _random_poly(rng, order)
+        outs, rows = op.interpolation_rows(face, sub, p, k, order, exact=True)
+        assert len(outs) == k * p * p
+        for o, row in zip(outs, rows):
+            assert sum(w * q(cpos[c]) for c, w in row.items()) == q(fpos[o])
+        outs, rows = op.restriction_rows(face, sub, p, k, order, exact=True)
+        assert len(outs) == k * (p // 3) ** 2
+        for o, row in zip(outs, rows):
+            assert sum(w * q(fpos[c]) for c, w in row.items()) == q(cpos[o])
