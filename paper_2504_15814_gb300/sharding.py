@@ -1,10 +1,14 @@
 """Splitting a transfer item list across GPUs.
 
 Transfer items are independent (every hanging face or subface reads its own
-coarse and fine face arrays and writes its own outputs), so N GPUs each take a
-contiguous, cost-balanced range of the items and run their own plan on local
-buffers: no collective is needed on the data path (weak scaling when every
-GPU keeps the same amount of work).
+coarse and fine face arrays and writes its own outputs), except that items
+naming the same coarse face array (subfaces of one hanging face) restrict
+into that one array and must stay together.  N GPUs each take a contiguous,
+cost-balanced range of the items that keeps such items together and run
+their own plan on local buffers: no collective is needed on the data path
+(weak scaling when every GPU keeps the same amount of work).  When the coarse
+and fine sides of a face live on different ranks, ``exchange`` moves the
+face arrays between them around the transfer.
 """
 import numpy as np
 
@@ -16,17 +20,42 @@ def item_cost(items):
     return nsub * items["overlap"].astype(np.int64) * items["patch_size"].astype(np.int64) ** 2 * items["order"]
 
 
+def allowed_cuts(items):
+    """Boolean array over cut positions 0..n: a cut at position c (ranks take
+    items [.., c) and [c, ..)) is allowed when no two items that share a
+    coarse face array lie on different sides of it.  Such items (subfaces of
+    one hanging face, listed separately) all restrict into the same coarse
+    array, so they must run on the same rank."""
+    n = len(items)
+    ok = np.ones(n + 1, dtype=bool)
+    if n == 0:
+        return ok
+    co = np.asarray(items["coarse_offset"], dtype=np.int64)
+    order = np.argsort(co, kind="stable")
+    sco = co[order]
+    starts = np.flatnonzero(np.concatenate([[True], sco[1:] != sco[:-1]]))
+    ends = np.concatenate([starts[1:], [n]])
+    for a, b in zip(starts, ends):
+        if b - a > 1:
+            members = order[a:b]
+            ok[members.min() + 1:members.max() + 1] = False
+    return ok
+
+
 def shard_bounds(items, world):
     """[lo_r, hi_r) item ranges of the world ranks, contiguous, balanced by
-    item_cost, covering every item exactly once (ranks may be empty)."""
+    item_cost, covering every item exactly once (ranks may be empty), never
+    separating items that share a coarse face array (see allowed_cuts)."""
     if world < 1:
         raise ValueError("world must be >= 1")
     prefix = np.concatenate([[0], np.cumsum(item_cost(items))]) if len(items) else np.zeros(1, dtype=np.int64)
     total = int(prefix[-1])
+    ok = allowed_cuts(items)
+    cand = np.flatnonzero(ok)
     bounds = [0]
     for r in range(1, world):
-        # the prefix whose cost is closest to r/world of the total
-        n = int(np.argmin(np.abs(prefix - total * r / world)))
+        # the allowed cut whose prefix cost is closest to r/world of the total
+        n = int(cand[np.argmin(np.abs(prefix[cand] - total * r / world))])
         bounds.append(min(max(n, bounds[-1]), len(items)))
     bounds.append(len(items))
     return [(bounds[r], bounds[r + 1]) for r in range(world)]
