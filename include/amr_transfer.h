@@ -23,8 +23,10 @@
  *   interface.  Subface s = s0 + 3 s1 (s0 along t0, s1 along t1) is the fine
  *   patch covering coarse tangential indices [s_t p/3, (s_t+1) p/3).
  *
- * Ownership: every data buffer is device memory owned by the caller; the
- * plan owns its device tables.  All calls that take a stream are
+ * Ownership: every data buffer is owned by the caller and lies in memory the
+ * device can access -- device memory, or pinned (page-locked) host memory,
+ * which the kernels then read and write in place; the plan owns its device
+ * tables.  All calls that take a stream are
  * asynchronous on that stream (NULL = the legacy default stream); argument
  * errors are detected on the host before anything is enqueued, and then
  * nothing is enqueued.  A plan is bound to the device that was current when
@@ -69,8 +71,29 @@ typedef enum {
   /* float64 base value u_c and float64-accurate stencil differences
      u_j - u_c; derivative and Taylor-increment arithmetic in float32 on those
      differences; the increment is added back to the float64 base.  Results
-     are float64; the error bound is data dependent (see DESIGN) */
-  AMR_PREC_SPLIT = 1
+     are float64.  The error is a few float32 roundings of the increment:
+     about 2^-22 times the largest |child - u_c| of a face, i.e. up to ~1e-6
+     of the field's magnitude on fields that vary by O(1) over one coarse
+     cell.  Taylor restriction keeps float64 accuracy (~1e-14).  Inputs must
+     lie in the float range: magnitudes below 2^-126 are taken as zero,
+     magnitudes of 2^128 and more give non-finite results (the injected,
+     coincident children excepted), a NaN propagates as NaN. */
+  AMR_PREC_SPLIT = 1,
+  /* Exact fixed point.  Per interpolation tile and unknown, every staged
+     coarse value is rounded once to an integer multiple of q = 3^g 2^-s, the
+     grid on which |value / q| < 2^47 for the largest magnitude of that
+     unknown in the tile's stencil region (g = 4, 2, 3 for Taylor-3, Taylor-2,
+     d-linear); differences, derivatives and the Taylor (or d-linear)
+     evaluation then run in exact int64 arithmetic, and each result is rounded
+     once to float64.  Error: at most (sum of |weights|) * q / 2, below 1e-13
+     of the region's largest magnitude; matches the float64 oracle to 1e-12
+     normwise.  Injected (coincident) children are copied exactly.  A region
+     holding a NaN or an infinity makes every other child of that unknown in
+     the tile NaN; results beyond the float64 range become infinite, below
+     its normal range +0; regions whose largest magnitude is below 2^-960
+     are quantized on the grid of 2^-960 instead.  Restriction and the
+     least-squares scheme use the float64 kernels. */
+  AMR_PREC_FIXED = 2
 } amr_precision;
 
 /* One transfer item: one subface (one fine patch, a 1/9 block of P and R,

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libamr_transfer.so")
 
 ABI_VERSION = 1
-PREC_FP64, PREC_SPLIT = 0, 1
+PREC_FP64, PREC_SPLIT, PREC_FIXED = 0, 1, 2
 SCHEME_FD, SCHEME_LS = 0, 1
 FLAG_CSR = 1
 ORDER_DLINEAR, ORDER_TAYLOR2, ORDER_TAYLOR3 = 1, 2, 3

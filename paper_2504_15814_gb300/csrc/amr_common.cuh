@@ -150,6 +150,12 @@ __host__ __device__ inline void interp_region(int p, int k, int order, int a0, i
 __host__ __device__ inline int wt_offset(int L) { return L == 3 ? 0 : (L == 4 ? 27 : 75); }
 constexpr int WT_SIZE = 150;
 
+// Denominator that makes every entry (L, pos, r, .) of the Taylor-coefficient
+// weight table an integer: 2 for the 3-point windows (Taylor-2 lines and all
+// mixed windows), 12, 24, 12 for r = 1, 2, 3 on the 4- and 5-point windows
+// of the Taylor-3 lines.
+__host__ __device__ inline int fixed_den(int L, int r) { return L == 3 ? 2 : (r == 2 ? 24 : 12); }
+
 // Least-squares line weights of the d-linear restriction, per overlap k,
 // coarse halo layer j < k and fine layer slot i < 3 (the fine patch's own
 // layers 0..k-1, or layers -1, 0 when k = 1).

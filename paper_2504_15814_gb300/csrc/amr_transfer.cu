@@ -13,6 +13,7 @@
 #include "adjoint_kernels.cuh"
 #include "csr_kernels.cuh"
 #include "transfer_kernels.cuh"
+#include "fixed_kernels.cuh"
 
 namespace {
 
@@ -49,6 +50,7 @@ amr_status upload_tables(int device) {
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw, t.rw, sizeof t.rw));
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw_hi, t.rw_hi, sizeof t.rw_hi));
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw_lo, t.rw_lo, sizeof t.rw_lo));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_fxw, t.fxw, sizeof t.fxw));
   g_tables_ready[device] = 1;
   return AMR_OK;
 }
@@ -61,7 +63,11 @@ amr_status upload(const std::vector<T>& h, T** d) {
   if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return AMR_ERR_OUT_OF_MEMORY; }
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   e = cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  if (e != cudaSuccess) {
+    cudaFree(*d);
+    *d = nullptr;
+    return cuda_fail(e, "cudaMemcpy");
+  }
   return AMR_OK;
 }
 
@@ -171,6 +177,16 @@ static amr_status ensure_adjoint(amr_transfer_plan* p) {
     return AMR_ERR_OUT_OF_MEMORY;
   }
   amr_status st;
+  auto drop = [&]() {
+    void** ptrs[] = {(void**)&p->pt_tiles_d, (void**)&p->rt_tiles_d, (void**)&p->group_ptr_d,
+                     (void**)&p->group_items_d, (void**)&p->item_class_d, (void**)&p->cls_pt_rows_d,
+                     (void**)&p->cls_rt_rows_d, (void**)&p->pt_row_ptr_d, (void**)&p->pt_col_d, (void**)&p->pt_val_d,
+                     (void**)&p->rt_row_ptr_d, (void**)&p->rt_col_d, (void**)&p->rt_val_d};
+    for (void** q : ptrs) {
+      cudaFree(*q);
+      *q = nullptr;
+    }
+  };
   if ((st = upload(ab.pt_tiles, &p->pt_tiles_d)) != AMR_OK || (st = upload(ab.rt_tiles, &p->rt_tiles_d)) != AMR_OK ||
       (st = upload(ab.group_ptr, &p->group_ptr_d)) != AMR_OK ||
       (st = upload(ab.group_items, &p->group_items_d)) != AMR_OK ||
@@ -179,8 +195,10 @@ static amr_status ensure_adjoint(amr_transfer_plan* p) {
       (st = upload(ab.cls_rt_rows, &p->cls_rt_rows_d)) != AMR_OK ||
       (st = upload(ab.pt.row_ptr, &p->pt_row_ptr_d)) != AMR_OK || (st = upload(ab.pt.col, &p->pt_col_d)) != AMR_OK ||
       (st = upload(ab.pt.val, &p->pt_val_d)) != AMR_OK || (st = upload(ab.rt.row_ptr, &p->rt_row_ptr_d)) != AMR_OK ||
-      (st = upload(ab.rt.col, &p->rt_col_d)) != AMR_OK || (st = upload(ab.rt.val, &p->rt_val_d)) != AMR_OK)
+      (st = upload(ab.rt.col, &p->rt_col_d)) != AMR_OK || (st = upload(ab.rt.val, &p->rt_val_d)) != AMR_OK) {
+    drop();
     return st;
+  }
   p->n_pt_tiles = (int)ab.pt_tiles.size();
   p->n_rt_tiles = (int)ab.rt_tiles.size();
   p->adj_ready = true;
@@ -224,7 +242,8 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
   d.flags = p->flags;
   amr::BuildResult br;
   try {
-    br = amr::build_plan(d, p->tuning.interp_smem_budget, p->tuning.interp_lanes == 32 ? 32 : 32767);
+    const bool per_warp = p->tuning.interp_lanes == 32 || p->precision == AMR_PREC_FIXED;
+    br = amr::build_plan(d, p->tuning.interp_smem_budget, per_warp ? 32 : 32767);
   } catch (const std::bad_alloc&) {
     return AMR_ERR_OUT_OF_MEMORY;
   }
@@ -244,6 +263,7 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
     cudaFree(it);
     cudaFree(rt);
     cudaFree(io);
+    cudaFree(itl);
     return st;
   }
   if (br.max_interp_smem > 48 * 1024) {
@@ -256,7 +276,11 @@ static amr_status rebuild_tiles(amr_transfer_plan* p) {
                          (const void*)amr::interp_kernel<false, 2, false, false, true>,
                          (const void*)amr::interp_kernel<false, 2, false, true, true>,
                          (const void*)amr::interp_kernel<true, 2, false, false, true>,
-                         (const void*)amr::interp_kernel<true, 2, false, true, true>};
+                         (const void*)amr::interp_kernel<true, 2, false, true, true>,
+                         (const void*)amr::interp_fixed_kernel<false, 0>, (const void*)amr::interp_fixed_kernel<false, 1>,
+                         (const void*)amr::interp_fixed_kernel<false, 2>, (const void*)amr::interp_fixed_kernel<false, 3>,
+                         (const void*)amr::interp_fixed_kernel<true, 0>, (const void*)amr::interp_fixed_kernel<true, 1>,
+                         (const void*)amr::interp_fixed_kernel<true, 2>, (const void*)amr::interp_fixed_kernel<true, 3>};
     cudaError_t e = cudaSuccess;
     for (size_t q = 0; q < sizeof fns / sizeof fns[0] && e == cudaSuccess; ++q)
       e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, br.max_interp_smem);
@@ -401,13 +425,25 @@ amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coa
   const int L = p->tuning.interp_lanes;
   const amr::Tile* seg = p->itiles_d;
   const bool split = p->precision == AMR_PREC_SPLIT;
+  const bool fixed = p->precision == AMR_PREC_FIXED;
   for (int q = 0; q < 4; seg += p->n_iseg[q], ++q) {
     if (p->n_iseg[q] == 0) continue;
     const dim3 g(p->n_iseg[q]);
     const int z = p->interp_smem;
     const amr_transfer_item* it = p->items_d;
     const int U = p->U;
-    if (q == 0 && split) {
+    if (q < 2 && fixed) {
+      switch (p->tuning.interp_addback + 4 * q) {
+        case 0: amr::interp_fixed_kernel<false, 0><<<g, b, z, s>>>(it, seg, U, coarse, fine); break;
+        case 1: amr::interp_fixed_kernel<false, 1><<<g, b, z, s>>>(it, seg, U, coarse, fine); break;
+        case 2: amr::interp_fixed_kernel<false, 2><<<g, b, z, s>>>(it, seg, U, coarse, fine); break;
+        case 3: amr::interp_fixed_kernel<false, 3><<<g, b, z, s>>>(it, seg, U, coarse, fine); break;
+        case 4: amr::interp_fixed_kernel<true, 0><<<g, b, z, s>>>(it, seg, U, coarse, fine); break;
+        case 5: amr::interp_fixed_kernel<true, 1><<<g, b, z, s>>>(it, seg, U, coarse, fine); break;
+        case 6: amr::interp_fixed_kernel<true, 2><<<g, b, z, s>>>(it, seg, U, coarse, fine); break;
+        default: amr::interp_fixed_kernel<true, 3><<<g, b, z, s>>>(it, seg, U, coarse, fine); break;
+      }
+    } else if (q == 0 && split) {
       switch (p->tuning.interp_addback) {
         case 0: amr::interp_kernel<true, 0><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L); break;
         case 1: amr::interp_kernel<true, 1><<<g, b, z, s>>>(it, seg, U, coarse, fine, nullptr, nullptr, L); break;
@@ -440,7 +476,8 @@ amr_status amr_transfer_plan_interpolate(amr_transfer_plan* p, const double* coa
 
 amr_status amr_transfer_plan_interpolate_increments(amr_transfer_plan* p, const double* coarse, float* increments,
                                                     void* stream) {
-  amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, increments, p ? p->info.increment_elems / 2 : 0);
+  // check_call counts 8-byte elements: the float32 increments take (n + 1) / 2 of them
+  amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, increments, p ? (p->info.increment_elems + 1) / 2 : 0);
   if (st != AMR_OK) return st;
   if (p->n_cpt > 0 || p->n_crt > 0) return AMR_ERR_UNSUPPORTED;  // increments come from the factorised kernel
   if (p->n_iseg[2] > 0 || p->n_iseg[3] > 0) return AMR_ERR_UNSUPPORTED;  // finite-difference items only
@@ -464,6 +501,10 @@ amr_status amr_transfer_plan_apply_increments(amr_transfer_plan* p, const double
   amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, fine, p ? p->fine_elems : 0);
   if (st != AMR_OK) return st;
   if (p->info.increment_elems > 0 && !increments) return AMR_ERR_INVALID_ARGUMENT;
+  const int64_t ibytes = p->info.increment_elems * 4;
+  if (increments && (ranges_overlap(increments, ibytes, fine, p->fine_elems * 8) ||
+                     ranges_overlap(increments, ibytes, coarse, p->coarse_elems * 8)))
+    return AMR_ERR_INVALID_ARGUMENT;
   if (p->n_cpt > 0 || p->n_crt > 0) return AMR_ERR_UNSUPPORTED;
   if (p->n_incr_tiles == 0) return AMR_OK;
   amr::apply_increments_kernel<<<p->n_incr_tiles, kThreads, 0, (cudaStream_t)stream>>>(
@@ -484,11 +525,11 @@ amr_status amr_transfer_plan_restrict(amr_transfer_plan* p, const double* fine, 
   }
   if (p->n_rtiles == 0) return AMR_OK;
   if (p->precision == AMR_PREC_SPLIT)
-    amr::restrict_kernel<true><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(p->items_d, p->rtiles_d, p->U,
-                                                                                  fine, coarse);
+    amr::restrict_kernel<amr::kRestrictSplit><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(
+        p->items_d, p->rtiles_d, p->U, fine, coarse);
   else
-    amr::restrict_kernel<false><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(p->items_d, p->rtiles_d, p->U,
-                                                                                   fine, coarse);
+    amr::restrict_kernel<amr::kRestrictF64><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(
+        p->items_d, p->rtiles_d, p->U, fine, coarse);
   AMR_CUDA(cudaGetLastError());
   return AMR_OK;
 }
@@ -533,7 +574,9 @@ amr_status amr_transfer_plan_get_tuning(const amr_transfer_plan* p, amr_transfer
 
 static bool tuning_valid(const amr_transfer_tuning& t, int precision) {
   auto ok_threads = [](int n, int max) { return n >= 32 && n <= max && n % 32 == 0; };
-  const int max_interp = precision == AMR_PREC_SPLIT ? amr::kMaxSplitInterpThreads : 256;
+  const int max_interp = precision == AMR_PREC_SPLIT   ? amr::kMaxSplitInterpThreads
+                         : precision == AMR_PREC_FIXED ? amr::kMaxFixedThreads
+                                                       : 256;
   return ok_threads(t.interp_threads, max_interp) && ok_threads(t.restrict_threads, 256) &&
          t.interp_smem_budget >= 4096 && t.interp_smem_budget <= 196 * 1024 && t.interp_addback >= 0 &&
          t.interp_addback <= 3 && (t.interp_lanes == 0 || t.interp_lanes == 32);
@@ -567,8 +610,12 @@ amr_status amr_transfer_plan_autotune(amr_transfer_plan* p, const double* coarse
   // common tile regions
   struct Shape { int lanes, threads, budget; };
   std::vector<Shape> shapes;
-  for (int th : {128, 256})
-    for (int kb : {24, 32, 48, 64, 96}) shapes.push_back({0, th, kb * 1024});
+  if (p->precision != AMR_PREC_FIXED)
+    for (int th : {128, 256})
+      for (int kb : {24, 32, 48, 64, 96}) shapes.push_back({0, th, kb * 1024});
+  if (p->precision == AMR_PREC_FIXED)
+    for (int th : {amr::kMaxFixedThreads / 2, amr::kMaxFixedThreads})
+      for (int kb : {64, 112}) shapes.push_back({32, th, kb * 1024});
   if (p->precision == AMR_PREC_SPLIT)
     for (int th : {256, amr::kMaxSplitInterpThreads})
       for (int kb : {64, 112}) shapes.push_back({32, th, kb * 1024});
@@ -590,7 +637,7 @@ amr_status amr_transfer_plan_autotune(amr_transfer_plan* p, const double* coarse
       best.interp_smem_budget = sh.budget;
     }
   }
-  if (p->precision == AMR_PREC_SPLIT) {
+  if (p->precision == AMR_PREC_SPLIT || p->precision == AMR_PREC_FIXED) {
     p->tuning = best;
     if ((st = rebuild_tiles(p)) != AMR_OK) return st;
     for (int mode = 0; mode <= 3; ++mode) {

@@ -72,6 +72,12 @@ Tables make_tables() {
           t.wt_interp[idx] = (c * scale).to_double();
           t.wt_restrict_f[idx] = (float)t.wt_restrict[idx];
           t.wt_interp_f[idx] = (float)t.wt_interp[idx];
+          const Q n = c * Q(fixed_den(L, r));
+          if (n.d != 1) {  // the fixed-point kernels rely on integral numerators
+            std::fprintf(stderr, "amr_transfer: non-integral stencil numerator (L %d, pos %d, r %d)\n", L, pos, r);
+            std::abort();
+          }
+          t.fxw[idx] = (int32_t)n.n;
         }
       }
   // Least-squares line through the fine patch's own layers (centres at
@@ -225,7 +231,7 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget, int nu_ca
     return fail(AMR_ERR_INVALID_ARGUMENT, "abi_version mismatch");
   if (desc.num_unknowns < 1) return fail(AMR_ERR_INVALID_ARGUMENT, "num_unknowns must be >= 1");
   if (desc.num_unknowns > 32767) return fail(AMR_ERR_UNSUPPORTED, "num_unknowns > 32767");
-  if (desc.precision != AMR_PREC_FP64 && desc.precision != AMR_PREC_SPLIT)
+  if (desc.precision != AMR_PREC_FP64 && desc.precision != AMR_PREC_SPLIT && desc.precision != AMR_PREC_FIXED)
     return fail(AMR_ERR_INVALID_ARGUMENT, "unknown precision");
   if (desc.flags & ~AMR_FLAG_CSR) return fail(AMR_ERR_INVALID_ARGUMENT, "unknown flags");
   if (desc.num_items < 0 || (desc.num_items > 0 && desc.items == nullptr))
@@ -291,16 +297,39 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget, int nu_ca
   // coarse centre may lie in two fine face arrays), finite-difference or
   // least-squares derivatives
   std::vector<Tile> seg[4];
+  auto region_vols = [](int p, int k, int m, int a0, int na, int b0, int nb) {
+    IRange rn, ra, rb;
+    interp_region(p, k, m, a0, na, b0, nb, rn, ra, rb);
+    return (int64_t)(rn.hi - rn.lo + 1) * (ra.hi - ra.lo + 1) * (rb.hi - rb.lo + 1);
+  };
   auto add_interp_tiles = [&](int64_t it, int sub, int slot, int alo, int ahi, int blo, int bhi, int p, int k, int m) {
-    std::vector<Tile>& dst = seg[(p % 3 ? 1 : 0) + (desc.items[it].scheme == 1 ? 2 : 0)];
-    for (int a0 = alo; a0 < ahi; a0 += TMAX)
-      for (int b0 = blo; b0 < bhi; b0 += TMAX) {
-        const int na = std::min(TMAX, ahi - a0), nb = std::min(TMAX, bhi - b0);
-        IRange rn, ra, rb;
-        interp_region(p, k, m, a0, na, b0, nb, rn, ra, rb);
-        const int64_t vols = (int64_t)(rn.hi - rn.lo + 1) * (ra.hi - ra.lo + 1) * (rb.hi - rb.lo + 1);
+    const bool ls = desc.items[it].scheme == 1;
+    std::vector<Tile>& dst = seg[(p % 3 ? 1 : 0) + (ls ? 2 : 0)];
+    // the fixed-point kernel stages 32 unknown slots per region volume
+    // (lane stride 32); its tiles shrink until the largest region fits the
+    // budget (at least one centre per tile)
+    const bool fixed = desc.precision == AMR_PREC_FIXED && !ls;
+    int ta = std::min(TMAX, ahi - alo), tb = std::min(TMAX, bhi - blo);
+    if (fixed) {
+      auto worst = [&](int na, int nb) {
+        int64_t v = 0;
+        for (int a0 = alo; a0 < ahi; a0 += na)
+          for (int b0 = blo; b0 < bhi; b0 += nb)
+            v = std::max(v, region_vols(p, k, m, a0, std::min(na, ahi - a0), b0, std::min(nb, bhi - b0)));
+        return v;
+      };
+      while ((ta > 1 || tb > 1) && worst(ta, tb) * 32 * 8 > smem_budget) {
+        if (ta >= tb) --ta;
+        else --tb;
+      }
+    }
+    for (int a0 = alo; a0 < ahi; a0 += ta)
+      for (int b0 = blo; b0 < bhi; b0 += tb) {
+        const int na = std::min(ta, ahi - a0), nb = std::min(tb, bhi - b0);
+        const int64_t vols = region_vols(p, k, m, a0, na, b0, nb);
         const int nu_max =
-            (int)std::min<int64_t>(std::min<int64_t>(U, nu_cap), std::max<int64_t>(1, smem_budget / (vols * 8)));
+            fixed ? (int)std::min<int64_t>(U, 32)
+                  : (int)std::min<int64_t>(std::min<int64_t>(U, nu_cap), std::max<int64_t>(1, smem_budget / (vols * 8)));
         const int nchunks = (int)((U + nu_max - 1) / nu_max);
         const int nu = (int)((U + nchunks - 1) / nchunks);
         for (int c = 0; c < nchunks; ++c) {
@@ -309,7 +338,7 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget, int nu_ca
           t.na = (int8_t)na; t.nb = (int8_t)nb; t.a0 = (int16_t)a0; t.b0 = (int16_t)b0;
           t.u0 = (int16_t)(c * nu); t.nu = (int16_t)std::min<int64_t>(nu, U - c * nu);
           dst.push_back(t);
-          r.max_interp_smem = std::max<int>(r.max_interp_smem, (int)(vols * t.nu * 8));
+          r.max_interp_smem = std::max<int>(r.max_interp_smem, (int)(vols * (fixed ? 32 : t.nu) * 8));
         }
       }
   };

@@ -26,6 +26,10 @@ struct Tables {
   double rw[RW_SIZE];     // combined restriction weights
   float rw_hi[RW_SIZE];   // float pair of the same: rw = rw_hi + rw_lo (+ O(2^-48))
   float rw_lo[RW_SIZE];
+  // exact integer numerators of the same Taylor-coefficient weights (lambda / r!,
+  // units of the coarse spacing): lambda / r! * fixed_den(L, r), fixed_den = 2
+  // for 3-point windows and 12, 24, 12 (r = 1, 2, 3) for 4- and 5-point windows
+  int32_t fxw[WT_SIZE];
 };
 
 // Built once per process.

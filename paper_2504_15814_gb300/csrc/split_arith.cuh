@@ -21,7 +21,8 @@ struct F2 {
 
 // x -> (hi, lo): hi keeps the sign, exponent and leading 24 significand bits
 // of x (truncation), lo the next 23 bits.  |x - hi - lo| < 2^-46 |x|.
-// |x| < 2^-126 gives (0, 0); |x| >= 2^128 gives hi = +-inf.
+// |x| < 2^-126 gives (0, 0); |x| >= 2^128 gives hi = +-inf; a NaN gives a
+// NaN hi, so that it propagates as NaN.
 __device__ __forceinline__ F2 split_f64(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const uint32_t h = (uint32_t)(b >> 32), l = (uint32_t)b;
@@ -34,7 +35,8 @@ __device__ __forceinline__ F2 split_f64(double x) {
     return r;
   }
   if (E > 1150) {
-    r.hi = __uint_as_float(sign | 0x7f800000u);
+    const bool nan = E == 2047 && ((h & 0xfffffu) | l) != 0u;
+    r.hi = __uint_as_float(sign | (nan ? 0x7fc00000u : 0x7f800000u));
     r.lo = 0.f;
     return r;
   }
@@ -58,7 +60,8 @@ __device__ __forceinline__ float two_sum(float a, float b, float& e) {
 // float64 value of s + e for a float pair with |e| <= ulp(s) (the output of
 // a TwoSum), assembled from the bit patterns: double(s) exactly, plus e in
 // units of the float64 ulp of s rounded to an integer.  Error <= 2^-53 |s|
-// beyond the rounding of e.  |s| < 2^-75 returns double(s) without e.
+// beyond the rounding of e.  |s| < 2^-75 returns double(s) without e; an
+// infinite or NaN s gives the float64 infinity or a NaN.
 __device__ __forceinline__ double pair_to_f64(float s, float e) {
   const uint32_t sb = __float_as_uint(s);
   const uint32_t E = (sb >> 23) & 0xffu;
@@ -69,6 +72,10 @@ __device__ __forceinline__ double pair_to_f64(float s, float e) {
   if (E == 0) {  // zero (or a float denormal, not produced here): signed zero
     hi = sb & 0x80000000u;
     lo = 0u;
+  }
+  if (E == 255u) {  // infinity or NaN: the float64 infinity or a NaN
+    hi = (sb & 0x80000000u) | 0x7ff00000u | ((mag & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)lo);
   }
   long long bits = ((long long)hi << 32) | lo;
   if (E >= 52u) {
@@ -104,7 +111,7 @@ __device__ __forceinline__ double add_back(F2 base, float incr) {
 
 // Exact float64 value of a float, assembled from its bits with integer
 // operations (float-to-double conversion runs on the float64 unit on GB300).
-// Float denormals become signed zero.
+// Float denormals become signed zero; infinities and NaNs stay so.
 __device__ __forceinline__ double f32_to_f64(float f) {
   const uint32_t b = __float_as_uint(f);
   const uint32_t mag = b & 0x7fffffffu;
@@ -114,6 +121,7 @@ __device__ __forceinline__ double f32_to_f64(float f) {
     hi = b & 0x80000000u;
     lo = 0u;
   }
+  if (mag >= 0x7f800000u) hi = (b & 0x80000000u) | 0x7ff00000u | ((mag & 0x7fffffu) >> 3);  // inf / NaN
   return __hiloint2double((int)hi, (int)lo);
 }
 

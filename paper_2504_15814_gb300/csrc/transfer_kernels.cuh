@@ -750,11 +750,17 @@ __device__ __forceinline__ void dlinear_restrict_split(const Fine& F, const Coar
   }
 }
 
-template <bool SPLIT>
+// Restriction precision modes: float64 throughout (float64 and fixed-point
+// plans), or split (float64 first extrapolated layer, float-pair deeper
+// layers, float32 d-linear averaging on exact float-pair differences).
+constexpr int kRestrictF64 = 0, kRestrictSplit = 1;
+
+template <int RP>
 __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* __restrict__ items,
                                                        const Tile* __restrict__ tiles, int U,
                                                        const double* __restrict__ fine,
                                                        double* __restrict__ coarse) {
+  constexpr bool SPLIT = RP == kRestrictSplit;
   const Tile t = tiles[blockIdx.x];
   const amr_transfer_item it = items[t.item];
   const int p = it.patch_size, k = it.overlap, m = it.order;

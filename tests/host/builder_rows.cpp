@@ -6,6 +6,9 @@
 //   builder_rows lsclass p k order sub          rows of P rebuilt from the
 //       least-squares class tables the interpolation kernel applies (slot
 //       layout of ls_interp_core)
+//   builder_rows tiles p k order sub precision U budget
+//       the interpolation tiles of one item (face 0) as "seg a0 na b0 nb u0
+//       nu region_volumes" lines, then "smem <bytes the launch provides>"
 #include <array>
 #include <cstdio>
 #include <cstdlib>
@@ -92,6 +95,35 @@ static void ls_class_rows(int M, int sub) {
       }
 }
 
+static void tiles(int M, int sub, int precision, int U, int budget) {
+  amr_transfer_item it{0, sub, P, K, M, 0, 0, 0};
+  amr_transfer_desc d{};
+  d.abi_version = AMR_TRANSFER_ABI_VERSION;
+  d.num_unknowns = U;
+  d.precision = precision;
+  d.num_items = 1;
+  d.items = &it;
+  d.coarse_elems = 2LL * K * P * P * U;
+  d.fine_elems = 9 * d.coarse_elems;
+  const BuildResult br = build_plan(d, budget, 32);
+  if (br.status != AMR_OK) {
+    std::printf("error %s\n", br.message.c_str());
+    return;
+  }
+  int64_t seg_end[4], acc = 0;
+  for (int q = 0; q < 4; ++q) seg_end[q] = (acc += br.interp_segments[q]);
+  for (size_t i = 0; i < br.interp_tiles.size(); ++i) {
+    const Tile& t = br.interp_tiles[i];
+    int seg = 0;
+    while ((int64_t)i >= seg_end[seg]) ++seg;
+    IRange rn, ra, rb;
+    interp_region(P, K, M, t.a0, t.na, t.b0, t.nb, rn, ra, rb);
+    const long vols = (long)(rn.hi - rn.lo + 1) * (ra.hi - ra.lo + 1) * (rb.hi - rb.lo + 1);
+    std::printf("%d %d %d %d %d %d %d %ld\n", seg, t.a0, t.na, t.b0, t.nb, t.u0, t.nu, vols);
+  }
+  std::printf("smem %d\n", br.max_interp_smem);
+}
+
 int main(int argc, char** argv) {
   if (argc < 6) return 2;
   P = std::atoi(argv[2]);
@@ -100,6 +132,7 @@ int main(int argc, char** argv) {
   if (!std::strcmp(argv[1], "interp")) print_rows(interpolation_rows(sub, 0, P, K, M, scheme));
   else if (!std::strcmp(argv[1], "restrict")) print_rows(restriction_rows(sub, 0, P, K, M, scheme));
   else if (!std::strcmp(argv[1], "lsclass")) ls_class_rows(M, sub);
+  else if (!std::strcmp(argv[1], "tiles") && argc > 8) tiles(M, sub, std::atoi(argv[6]), std::atoi(argv[7]), std::atoi(argv[8]));
   else return 2;
   return 0;
 }

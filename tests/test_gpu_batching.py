@@ -45,7 +45,7 @@ def _operators(plan, c, f):
     return fd.cpu().numpy(), co.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision,tol", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6)])
+@pytest.mark.parametrize("precision,tol", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6), (B.PREC_FIXED, 1e-12)])
 @pytest.mark.parametrize("shape", [(128, 8192, 128, 0, 0), (256, 24 * 1024, 64, 1, 0), (64, 100 * 1024, 256, 3, 0),
                                    (256, 64 * 1024, 256, 2, 0), (256, 112 * 1024, 128, 2, 32),
                                    (64, 16 * 1024, 256, 1, 32), (384, 64 * 1024, 256, 3, 32)])
@@ -53,7 +53,7 @@ def test_set_tuning_keeps_parity(shape, precision, tol):
     U = 13
     items, c, f = _batch(U=U)
     plan = B.Plan(items, U, len(c), len(f), precision)
-    if precision == B.PREC_FP64 and shape[0] > 256:  # the float64 kernel's CTA is at most 256 threads
+    if precision != B.PREC_SPLIT and shape[0] > 256:  # float64 and fixed-point CTAs hold at most 256 threads
         with pytest.raises(B.AmrError):
             plan.set_tuning(*shape)
         return
@@ -72,7 +72,7 @@ def test_invalid_tuning_rejected():
             plan.set_tuning(*bad)
 
 
-@pytest.mark.parametrize("precision,tol", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6)])
+@pytest.mark.parametrize("precision,tol", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6), (B.PREC_FIXED, 1e-12)])
 def test_autotune_and_step_graph(precision, tol):
     U = 13
     items, c, f = _batch(n=12, U=U, seed=4)

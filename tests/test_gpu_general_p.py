@@ -19,7 +19,7 @@ from .test_gpu_parity import FP64_TOL, SPLIT_BOUND, _batch, _check
 
 pytestmark = pytest.mark.gpu
 
-PRECISIONS = [(B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND)]
+PRECISIONS = [(B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND), (B.PREC_FIXED, FP64_TOL)]
 
 
 @pytest.mark.parametrize("precision,tol", PRECISIONS)

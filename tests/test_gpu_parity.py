@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
 same seeded inputs, element by element.
 
-FP64 path: normwise relative error per (item, unknown) <= 1e-12.
+FP64 path and the exact fixed-point path: normwise relative error per
+(item, unknown) <= 1e-12.
 Split path: the float32 derivative/increment arithmetic on float64
 differences gives an error below SPLIT_BOUND on the smooth synthetic fields
 (derived bound: a few float32 roundings of the increment, ~1e-7 of it, and the
@@ -20,6 +21,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 SPLIT_BOUND = 2e-6
+PRECISIONS = [(B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND), (B.PREC_FIXED, FP64_TOL)]
 
 
 def _batch(faces, subs, ps, ks, orders, U, seed=0):
@@ -32,15 +34,27 @@ def _batch(faces, subs, ps, ks, orders, U, seed=0):
     return items, coarse.numpy(), fine.numpy()
 
 
+_REFS = {}
+
+
+def _references(items, U, coarse, fine):
+    """Oracle results and written masks for one input set, computed once per
+    test run (several precisions are checked against the same references)."""
+    key = (items.tobytes(), U, coarse.tobytes()[:4096], len(coarse), len(fine))
+    if key not in _REFS:
+        _REFS.clear()
+        fmask, cmask = written_masks(items, U, len(coarse), len(fine))
+        _REFS[key] = (fmask, cmask, tr.interpolate(items, U, coarse, fine), tr.restrict(items, U, fine, coarse))
+    return _REFS[key]
+
+
 def _check(items, U, coarse, fine, precision, tol):
-    fmask, cmask = written_masks(items, U, len(coarse), len(fine))
+    fmask, cmask, f_ref, c_ref = _references(items, U, coarse, fine)
     plan = B.Plan(items, U, len(coarse), len(fine), precision)
-    f_ref = tr.interpolate(items, U, coarse, fine)
     f_gpu = gpu_interpolate(plan, coarse, fine)
     # entries interpolate must not touch are bit-identical
     assert np.array_equal(f_gpu[~fmask], fine[~fmask])
     e_i, rms_i = normwise_errors(items, U, f_gpu, f_ref, fmask, "fine")
-    c_ref = tr.restrict(items, U, fine, coarse)
     c_gpu = gpu_restrict(plan, fine, coarse)
     assert np.array_equal(c_gpu[~cmask], coarse[~cmask])
     e_r, rms_r = normwise_errors(items, U, c_gpu, c_ref, cmask, "coarse")
@@ -52,7 +66,7 @@ def _check(items, U, coarse, fine, precision, tol):
     return e_i, e_r
 
 
-@pytest.mark.parametrize("precision,tol", [(B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND)])
+@pytest.mark.parametrize("precision,tol", PRECISIONS)
 @pytest.mark.parametrize("order", [1, 2, 3])
 def test_whole_faces_all_orientations(order, precision, tol):
     # 12 hanging faces, all six orientations twice, p = 9, k = 3, U = 59
@@ -62,7 +76,7 @@ def test_whole_faces_all_orientations(order, precision, tol):
     _check(items, 59, c, f, precision, tol)
 
 
-@pytest.mark.parametrize("precision,tol", [(B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND)])
+@pytest.mark.parametrize("precision,tol", PRECISIONS)
 @pytest.mark.parametrize("order", [1, 2, 3])
 @pytest.mark.parametrize("p,k", [(6, 2), (6, 3), (12, 2), (12, 3)])
 def test_subface_items(order, p, k, precision, tol):
@@ -90,6 +104,7 @@ def test_mixed_batch_and_large_patches():
     subs = rng.integers(-1, 9, n)
     items, c, f = _batch(faces, subs, ps, ks, orders, 5, seed=7)
     _check(items, 5, c, f, B.PREC_FP64, FP64_TOL)
+    _check(items, 5, c, f, B.PREC_FIXED, FP64_TOL)
 
 
 def test_single_face_quadratic_exact():
@@ -143,7 +158,7 @@ def test_full_size_uniform_batch_sampled():
     against the oracle, one by one."""
     items, coarse, fine = wl.uniform_batch(device="cuda")
     U = 59
-    for precision, tol in ((B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND)):
+    for precision, tol in ((B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND), (B.PREC_FIXED, FP64_TOL)):
         plan = B.Plan(items, U, coarse.numel(), fine.numel(), precision)
         tuned = plan.autotune(coarse, fine.clone(), coarse.clone())
         record(test="full_size_sampled_tuning", precision=precision, **tuned)

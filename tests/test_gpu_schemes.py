@@ -62,7 +62,7 @@ def test_mixed_fd_and_ls_items_in_one_plan():
     _check(items, 7, c, f, B.PREC_FP64, 1e-12, 1e-12, tag="mixed")
 
 
-@pytest.mark.parametrize("precision,tol_i", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6)])
+@pytest.mark.parametrize("precision,tol_i", [(B.PREC_FP64, 1e-12), (B.PREC_SPLIT, 2e-6), (B.PREC_FIXED, 1e-12)])
 @pytest.mark.parametrize("order", [1, 2, 3])
 def test_csr_flag_reproduces_factorised_operators(order, precision, tol_i):
     items, c, f = _batch([order] * 12, [0] * 12, seed=11)

@@ -79,3 +79,39 @@ def test_least_squares_class_tables_match_oracle(harness, p, k, order, sub):
     give the oracle's least-squares interpolation rows."""
     outs, rows = op.interpolation_rows(0, sub, p, k, order, scheme=op.SCHEME_LS)
     assert _worst(_rows(harness, "lsclass", p, k, order, sub), outs, rows) < 1e-13
+
+
+@pytest.mark.parametrize("p,k,order,sub", [(9, 3, 3, -1), (12, 3, 3, -1), (6, 2, 2, -1), (16, 3, 3, 4), (24, 3, 1, -1),
+                                           (48, 3, 3, -1), (7, 3, 3, -1), (4, 2, 3, 0), (9, 1, 1, -1)])
+@pytest.mark.parametrize("budget", [64 * 1024, 112 * 1024])
+def test_fixed_point_tiles_fit_their_launch(harness, p, k, order, sub, budget):
+    """Fixed-point plans (precision 2): every tile of the fixed-point kernel
+    carries at most 32 unknowns and its region, at 32 slots of 8 bytes per
+    volume, fits the shared memory the launch provides (and the budget,
+    unless a single centre's region exceeds it); the tiles cover every
+    coarse centre of the item once per unknown."""
+    U = 59
+    out = subprocess.run([harness, "tiles", *map(str, (p, k, order, sub, 2, U, budget))], check=True, capture_output=True,
+                         text=True).stdout.split("\n")
+    smem = int([line for line in out if line.startswith("smem")][0].split()[1])
+    cover = collections.Counter()
+    for line in out:
+        if not line or line.startswith("smem"):
+            continue
+        seg, a0, na, b0, nb, u0, nu, vols = map(int, line.split())
+        assert seg in (0, 1) and 1 <= nu <= 32
+        assert vols * 32 * 8 <= smem <= 227 * 1024
+        if na * nb > 1:
+            assert vols * 32 * 8 <= budget
+        for a in range(a0, a0 + na):
+            for b in range(b0, b0 + nb):
+                for u in range(u0, u0 + nu):
+                    cover[(a, b, u)] += 1
+    if sub < 0:
+        lo_a, hi_a, lo_b, hi_b = 0, p, 0, p
+    else:
+        s0, s1 = sub % 3, sub // 3
+        lo_a, hi_a = (s0 * p) // 3, (s0 * p + p - 1) // 3 + 1
+        lo_b, hi_b = (s1 * p) // 3, (s1 * p + p - 1) // 3 + 1
+    assert set(cover.values()) == {1}
+    assert len(cover) == (hi_a - lo_a) * (hi_b - lo_b) * U
