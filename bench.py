@@ -37,9 +37,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["split", "fp64"], default="split")
+    ap.add_argument("--precision", choices=["fixed", "split", "fp64"], default="fixed")
     ap.add_argument("--faces", type=int, default=N_FACES)
     ap.add_argument("--no-extra", action="store_true", help="skip the d-linear / Taylor-2 / e2e / oracle legs")
+    ap.add_argument("--tuning", default=None,
+                    help="launch shape threads,smem_budget,restrict_threads,addback,lanes instead of autotuning")
+    ap.add_argument("--order", type=int, default=3, choices=[1, 2, 3], help="operator order of the timed step")
     return ap.parse_args()
 
 
@@ -118,10 +121,10 @@ def kernel_source_hash():
 
 
 def profiled_traffic(kernel, faces):
-    """DRAM bytes per launch of a kernel from a committed ncu summary, scaled
-    to `faces` hanging faces, when the summary was taken on these exact
-    sources (else None)."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_uniform_batch_split.md")
+    """DRAM bytes per launch of a kernel from a committed ncu summary
+    (profiles/<kernel>_uniform_batch.md), scaled to `faces` hanging faces,
+    when the summary was taken on these exact sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_uniform_batch.md")
     try:
         text = open(path).read()
     except OSError:
@@ -176,23 +179,86 @@ def oracle_sample(items, coarse, fine, n_faces, U):
     return sub, c, f
 
 
-def time_oracle(sub, c, f, U, budget_s=10.0):
-    """Oracle interpolate + restrict on the sample; operators are built
-    before timing (construction happens once per plan on the GPU side too)."""
+def _oracle_worker(conn, U):
+    """Pool process: receives its share of the sampled faces once, builds the
+    operators (construction happens once per plan on the GPU side too), then
+    runs one interpolate + restrict per "go" message."""
+    import numpy as np
     from oracle import transfer as tr
-    tr.restrict(sub[:6], U, f, c)
-    tr.interpolate(sub[:6], U, c, f)
-    reps, t0 = 0, time.perf_counter()
-    while True:
+    sub, c, f = conn.recv()
+    if len(sub):
+        tr.restrict(sub, U, tr.interpolate(sub, U, c, f), c)
+    conn.send("ready")
+    while conn.recv() == "go":
         f2 = tr.interpolate(sub, U, c, f)
         tr.restrict(sub, U, f2, c)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or reps >= 3:
-            break
+        conn.send(len(sub))
+
+
+def oracle_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """The CPU oracle over all host cores: one process per core (spawn
+    context, safe after CUDA initialisation), each holding a contiguous share
+    of the sampled faces; a step runs every share once in parallel."""
+
+    def __init__(self, U, sub, c, f):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.cores = oracle_cores()
+        n = len(sub)
+        arr = 2 * K * P * P * U
+        self.procs, self.conns = [], []
+        for r in range(self.cores):
+            lo, hi = r * n // self.cores, (r + 1) * n // self.cores
+            s2 = sub[lo:hi].copy()
+            s2["coarse_offset"] -= lo * arr
+            s2["fine_offset"] -= lo * 9 * arr
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_worker, args=(b, U), daemon=True)
+            pr.start()
+            a.send((s2, c[lo * arr:hi * arr].copy(), f[lo * 9 * arr:hi * 9 * arr].copy()))
+            self.procs.append(pr)
+            self.conns.append(a)
+        for a in self.conns:
+            a.recv()
+
+    def step(self):
+        for a in self.conns:
+            a.send("go")
+        return sum(a.recv() for a in self.conns)
+
+    def close(self):
+        for a in self.conns:
+            a.send("stop")
+        for pr in self.procs:
+            pr.join()
+
+
+def time_oracle(sub, c, f, U, budget_s=15.0):
+    """Oracle interpolate + restrict of the sampled faces on all host cores;
+    operators are built before timing.  Returns (volume-unknowns/s, seconds
+    per pass, cores)."""
+    pool = OraclePool(U, sub, c, f)
+    try:
+        pool.step()  # warm-up
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            pool.step()
+            reps += 1
+            el = time.perf_counter() - t0
+            if el > budget_s or reps >= 3:
+                break
+    finally:
+        pool.close()
     per = el / reps
     outs = len(sub) * (9 * K * P * P + K * P * P) * U
-    return outs / per, per
+    return outs / per, per, pool.cores
 
 
 def run_reference(args):
@@ -203,19 +269,18 @@ def run_reference(args):
     from paper_2504_15814_gb300 import workloads as wl
     if int(os.environ.get("RANK", "0")) != 0:
         return
-    n_sample = 64
+    cores = oracle_cores()
+    n_sample = 4 * cores  # four hanging faces per host core
     items, coarse, fine = wl.uniform_batch(n_faces=n_sample, p=P, k=K, U=U, order=3, config_index=1)
-    from oracle import transfer as tr
-    tr.interpolate(items[:6], U, coarse.numpy(), fine.numpy())
-    tr.restrict(items[:6], U, fine.numpy(), coarse.numpy())
-    times = []
     c, f = coarse.numpy(), fine.numpy()
+    pool = OraclePool(U, items, c, f)  # operators built in the workers before timing
+    times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        f2 = tr.interpolate(items, U, c, f)
-        tr.restrict(items, U, f2, c)
+        pool.step()
         if s >= args.warmup:
             times.append(time.perf_counter() - t0)
+    pool.close()
     per = sum(times) / len(times)
     outs = n_sample * (9 * K * P * P + K * P * P) * U
     value = outs / per
@@ -225,8 +290,9 @@ def run_reference(args):
             "config": {"workload": f"uniform batch sample: {n_sample} hanging faces of the 2048-face batch, "
                                    f"p={P}, k={K}, U={U}, Taylor-3 interpolate+restrict",
                        "faces": n_sample, "p": P, "k": K, "U": U},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n_sample} hanging faces per step (scipy CSR apply, single thread)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                             "sample": f"{n_sample} hanging faces of the batch per step, Taylor-3 interpolate + "
+                                       f"restrict, scipy CSR apply, one process per host core"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -243,15 +309,19 @@ def main():
     dist, rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = B.PREC_SPLIT if args.precision == "split" else B.PREC_FP64
+    prec = {"fixed": B.PREC_FIXED, "split": B.PREC_SPLIT, "fp64": B.PREC_FP64}[args.precision]
     # weak scaling: a global batch of faces-per-GPU x N faces, each rank
     # keeping its cost-balanced shard (items are independent: no collective)
-    items, coarse, fine = wl.uniform_batch(n_faces=args.faces * world, p=P, k=K, U=U, order=3, config_index=1,
-                                           device=dev, shard=(rank, world) if world > 1 else None)
+    items, coarse, fine = wl.uniform_batch(n_faces=args.faces * world, p=P, k=K, U=U, order=args.order,
+                                           config_index=1, device=dev, shard=(rank, world) if world > 1 else None)
     coarse_out = coarse.clone()
     plan = B.Plan(items, U, coarse.numel(), fine.numel(), prec)
     stream = torch.cuda.current_stream(dev)
-    tuning = plan.autotune(coarse, fine, coarse_out)  # launch shapes for this GPU, before timing
+    if args.tuning:
+        plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
+        tuning = plan.tuning
+    else:
+        tuning = plan.autotune(coarse, fine, coarse_out)  # launch shapes for this GPU, before timing
     info = plan.info
 
     def step():
@@ -295,23 +365,28 @@ def main():
     hbm_peak = float(peaks["hbm_gbs"])
     interp_gbs = info["interp_bytes"] / (t_interp * 1e-3) / 1e9
     restrict_gbs = info["restrict_bytes"] / (t_restrict * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "interp_kernel", "achieved": interp_gbs, "peak": hbm_peak,
+    ikern = {B.PREC_FIXED: "interp_fixed_kernel", B.PREC_SPLIT: "interp_kernel_split",
+             B.PREC_FP64: "interp_kernel_fp64"}[prec]
+    rkern = "restrict_kernel_split" if prec == B.PREC_SPLIT else "restrict_kernel_fp64"
+    roofline = {"bound": "hbm", "kernel": ikern, "achieved": interp_gbs, "peak": hbm_peak,
                 "unit": "GB/s", "frac": interp_gbs / hbm_peak,
-                "traffic": profiled_traffic("interp_kernel", args.faces) if prec == B.PREC_SPLIT else None,
+                "traffic": profiled_traffic(ikern, args.faces),
                 "algorithmic_bytes_per_launch": info["interp_bytes"], "launch_ms": t_interp,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "restrict_kernel": {"achieved": restrict_gbs, "frac": restrict_gbs / hbm_peak,
                                     "launch_ms": t_restrict, "algorithmic_bytes_per_launch": info["restrict_bytes"],
-                                    "traffic": profiled_traffic("restrict_kernel", args.faces)
-                                    if prec == B.PREC_SPLIT else None}}
+                                    "kernel": rkern, "traffic": profiled_traffic(rkern, args.faces)}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == B.PREC_FP64 else "f64 base / f32 increment",
+            "vs_baseline": None,
+            "dtype": {B.PREC_FIXED: "int64 interpolation, f64 restriction", B.PREC_SPLIT: "f64 base / f32 increment",
+                      B.PREC_FP64: "f64"}[prec],
             "data": "synthetic",
             "config": {"workload": f"uniform batch: {args.faces} hanging faces per GPU, p={P}, k={K}, U={U}, "
-                                   f"FP64 AoS, Taylor-3 interpolate+restrict",
-                       "faces_per_gpu": args.faces, "p": P, "k": K, "U": U, "order": 3,
+                                   f"FP64 AoS, {['d-linear', 'Taylor-2', 'Taylor-3'][args.order - 1]} "
+                                   "interpolate+restrict",
+                       "faces_per_gpu": args.faces, "p": P, "k": K, "U": U, "order": args.order,
                        "precision": args.precision, "parallelism": f"dp{world}" if world > 1 else "single GPU",
                        "tuning": tuning,
                        "l2": f"inputs ({(coarse.numel() + fine.numel()) * 8 / 1e9:.1f} GB) larger than L2, "
@@ -325,11 +400,13 @@ def main():
         line["e2e"] = e2e_zero_copy(plan, items, coarse, fine, coarse_out, outs, stream)
         line["e2e"]["staged_copies"] = staged
         line["err_vs_fp64"] = error_vs_oracle(items, coarse, fine, plan, U)
-        sub, c_h, f_h = oracle_sample(items, coarse, fine, 32, U)
-        v, per = time_oracle(sub, c_h, f_h, U)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "32 hanging faces of the batch, Taylor-3 interpolate+restrict, "
-                                          "operators prebuilt, scipy CSR apply (single thread)"}
+        n_cpu = 4 * oracle_cores()
+        sub, c_h, f_h = oracle_sample(items, coarse, fine, n_cpu, U)
+        v, per, cores = time_oracle(sub, c_h, f_h, U)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{n_cpu} hanging faces of the batch (4 per host core), Taylor-3 "
+                                          "interpolate + restrict, operators prebuilt, scipy CSR apply, one "
+                                          "process per host core"}
         line["workloads"] = other_workloads(B, wl, stream)
     plan.close()
     if rank == 0:
@@ -456,7 +533,7 @@ def other_workloads(B, wl, stream):
     items, coarse, fine = wl.uneven_batch(device="cuda")
     U = 59
     co = coarse.clone()
-    for prec_name, prec in (("split", B.PREC_SPLIT), ("fp64", B.PREC_FP64)):
+    for prec_name, prec in (("fixed", B.PREC_FIXED), ("split", B.PREC_SPLIT), ("fp64", B.PREC_FP64)):
         plan = B.Plan(items, U, coarse.numel(), fine.numel(), prec)
         info = plan.info
         outs = (info["interp_outputs"] + info["restrict_outputs"]) * U
@@ -477,7 +554,7 @@ def other_workloads(B, wl, stream):
     items, coarse, fine = wl.puncture_batch(device="cuda")
     co = coarse.clone()
     res = {"workload": "8,192 hanging faces, p=9, k=3, U=59, Taylor-3, puncture-like fields"}
-    for prec_name, prec in (("split", B.PREC_SPLIT), ("fp64", B.PREC_FP64)):
+    for prec_name, prec in (("fixed", B.PREC_FIXED), ("split", B.PREC_SPLIT), ("fp64", B.PREC_FP64)):
         plan = B.Plan(items, U, coarse.numel(), fine.numel(), prec)
         info = plan.info
         fo = fine.clone()
@@ -525,10 +602,11 @@ def other_workloads(B, wl, stream):
 
 
 def compare_paths(B, wl, items, coarse, fine, coarse_out, U, args, stream, plan_main):
-    """d-linear and Taylor-2 on the same workload and GPU, FP64 and split."""
+    """d-linear and Taylor-2 on the same workload and GPU, in every precision
+    mode, with the error of each against the FP64 oracle."""
     out = {}
     for name, order in (("dlinear", 1), ("taylor2", 2), ("taylor3", 3)):
-        for prec_name, prec in (("fp64", B.PREC_FP64), ("split", B.PREC_SPLIT)):
+        for prec_name, prec in (("fixed", B.PREC_FIXED), ("fp64", B.PREC_FP64), ("split", B.PREC_SPLIT)):
             it = items.copy()
             it["order"] = order
             plan = B.Plan(it, U, coarse.numel(), fine.numel(), prec)
@@ -553,7 +631,8 @@ def compare_paths(B, wl, items, coarse, fine, coarse_out, U, args, stream, plan_
                 "value": outs / (ms * 1e-3), "ms_per_step": ms, "interp_ms": ti, "restrict_ms": tr_,
                 "interp_gbs": info["interp_bytes"] / (ti * 1e-3) / 1e9,
                 "restrict_gbs": info["restrict_bytes"] / (tr_ * 1e-3) / 1e9,
-                "step_gbs": (info["interp_bytes"] + info["restrict_bytes"]) / (ms * 1e-3) / 1e9}
+                "step_gbs": (info["interp_bytes"] + info["restrict_bytes"]) / (ms * 1e-3) / 1e9,
+                "err_vs_fp64": error_vs_oracle(it, coarse, fine, plan, U, n_faces=4)}
             plan.close()
     return out
 
@@ -695,7 +774,7 @@ def e2e_zero_copy(plan, items, coarse, fine, coarse_out, outs, stream, chunk_cou
                    "writes); chunks of faces overlap restriction with the next chunk's interpolation"}
 
 
-def error_vs_oracle(items, coarse, fine, plan, U, n=400):
+def error_vs_oracle(items, coarse, fine, plan, U, n_faces=8):
     """Max and RMS normwise error of sampled outputs against the FP64 oracle."""
     import numpy as np
     import torch
@@ -708,7 +787,7 @@ def error_vs_oracle(items, coarse, fine, plan, U, n=400):
     rng = np.random.default_rng(5)
     arr = 2 * K * P * P * U
     errs = []
-    chosen = rng.choice(len(items), 8, replace=False)
+    chosen = rng.choice(len(items), n_faces, replace=False)
     for i in chosen:
         it = items[int(i)]
         co, fo = int(it["coarse_offset"]), int(it["fine_offset"])
@@ -727,7 +806,7 @@ def error_vs_oracle(items, coarse, fine, plan, U, n=400):
             errs.append((np.abs(g - r).max(axis=0) / np.maximum(np.abs(r).max(axis=0), 1e-300)))
     e = np.concatenate(errs)
     return {"max": float(e.max()), "rms": float(np.sqrt(np.mean(e ** 2))),
-            "sample": "8 random hanging faces, all outputs, normwise per (face, unknown)"}
+            "sample": f"{n_faces} random hanging faces, all outputs, normwise per (face, unknown)"}
 
 
 if __name__ == "__main__":
