@@ -585,16 +585,29 @@ def other_workloads(B, wl, stream):
     out["puncture_split"] = res
     del items, coarse, fine, co
     torch.cuda.empty_cache()
-    # adjoint: 4,096 faces, Taylor-3, P^T and R^T
+    # adjoint: 4,096 faces, Taylor-3, P^T and R^T; algorithmic bytes: P^T reads
+    # the ghost gradients and writes the whole coarse arrays, R^T reads the
+    # restricted halo gradients and writes the whole fine arrays (the API
+    # overwrites every gradient entry)
     items, coarse, fine = wl.uniform_batch(n_faces=4096, U=U, order=3, config_index=4, device="cuda")
-    plan = B.Plan(items, U, coarse.numel(), fine.numel(), B.PREC_FP64)
+    plan = B.Plan(items, U, coarse.numel(), fine.numel(), B.PREC_FIXED)
     gc, gf = torch.empty_like(coarse), torch.empty_like(fine)
     plan.interpolate_adjoint(fine, gc)  # builds the transposed tables
     t = _time_steps(lambda: (plan.interpolate_adjoint(fine, gc), plan.restrict_adjoint(coarse, gf)), 5, stream)
-    info = plan.info
-    out["adjoint"] = {"workload": "4,096 hanging faces, p=9, k=3, U=59, Taylor-3, P^T + R^T (float64)",
+    t_pt = time_kernel(lambda: plan.interpolate_adjoint(fine, gc), 5, stream)
+    t_rt = time_kernel(lambda: plan.restrict_adjoint(coarse, gf), 5, stream)
+    nf = 4096
+    b_pt = nf * (9 * K * P * P + 2 * K * P * P) * U * 8
+    b_rt = nf * (K * P * P + 18 * K * P * P) * U * 8
+    hbm = float(measured_peaks()[0]["hbm_gbs"])
+    out["adjoint"] = {"workload": "4,096 hanging faces, p=9, k=3, U=59, Taylor-3, P^T + R^T",
                       "ms_per_step": t, "value": (coarse.numel() + fine.numel()) / (t * 1e-3),
-                      "unit": "gradient entries/s"}
+                      "unit": "gradient entries/s",
+                      "interp_adjoint_ms": t_pt, "restrict_adjoint_ms": t_rt,
+                      "algorithmic_bytes": b_pt + b_rt, "achieved_gbs": (b_pt + b_rt) / (t * 1e-3) / 1e9,
+                      "frac": (b_pt + b_rt) / (t * 1e-3) / 1e9 / hbm,
+                      "interp_adjoint_gbs": b_pt / (t_pt * 1e-3) / 1e9,
+                      "restrict_adjoint_gbs": b_rt / (t_rt * 1e-3) / 1e9}
     plan.close()
     del items, coarse, fine, gc, gf
     torch.cuda.empty_cache()

@@ -156,15 +156,21 @@ amr_status amr_transfer_plan_restrict(amr_transfer_plan* plan, const double* fin
 /* g_coarse = P^T g_fine over the whole coarse buffer: overwrites all
  * coarse_elems values (zero where no weight reaches) and sums the
  * contributions of items that share a coarse face array.  Only the ghost
- * entries of g_fine are read.  Always float64.  The first adjoint call on a
- * plan builds its transposed-operator tables (host work and a synchronous
- * upload): make it before capturing a stream. */
+ * entries of g_fine are read.  Float64 results for every plan precision:
+ * groups of items sharing a coarse array whose items all use
+ * finite-difference stencils with p a multiple of 3 run the factorised
+ * transpose in exact fixed point (the ghost gradients of the group rounded
+ * once onto a grid of 2^-44 of their largest magnitude per unknown, then
+ * exact integer sums; a group holding a NaN or an infinity gives NaN for that
+ * unknown); the other items use explicit transposed rows in float64.  The
+ * first adjoint call on a plan builds its transposed-operator tables (host
+ * work and a synchronous upload): make it before capturing a stream. */
 amr_status amr_transfer_plan_interpolate_adjoint(amr_transfer_plan* plan, const double* g_fine,
                                                  double* g_coarse, void* cuda_stream);
 
 /* g_fine = R^T g_coarse over the whole fine buffer: overwrites all
  * fine_elems values (zero where no weight reaches).  Only the entries of
- * g_coarse that restriction writes are read.  Always float64. */
+ * g_coarse that restriction writes are read.  Float64 arithmetic. */
 amr_status amr_transfer_plan_restrict_adjoint(amr_transfer_plan* plan, const double* g_coarse,
                                               double* g_fine, void* cuda_stream);
 

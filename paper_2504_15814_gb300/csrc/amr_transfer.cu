@@ -14,6 +14,7 @@
 #include "csr_kernels.cuh"
 #include "transfer_kernels.cuh"
 #include "fixed_kernels.cuh"
+#include "fixed_adjoint.cuh"
 
 namespace {
 
@@ -136,6 +137,9 @@ struct amr_transfer_plan {
   bool adj_ready = false;
   int n_pt_tiles = 0, n_rt_tiles = 0;
   amr::AdjointTile *pt_tiles_d = nullptr, *rt_tiles_d = nullptr;
+  int n_fx_pt_tiles = 0, n_rtt_tiles = 0, fx_adj_smem = 0;
+  amr::AdjointTile* fx_pt_tiles_d = nullptr;
+  amr::Tile* rtt_tiles_d = nullptr;
   int32_t *group_ptr_d = nullptr, *group_items_d = nullptr, *item_class_d = nullptr;
   int32_t *cls_pt_rows_d = nullptr, *cls_rt_rows_d = nullptr, *pt_row_ptr_d = nullptr, *rt_row_ptr_d = nullptr;
   uint32_t *pt_col_d = nullptr, *rt_col_d = nullptr;
@@ -155,7 +159,8 @@ static void free_plan(amr_transfer_plan* p) {
   for (void* q : csr) cudaFree(q);
   void* ls[] = {p->ls_wf_d, p->ls_wd_d, p->ls_off_d};
   for (void* q : ls) cudaFree(q);
-  void* ptrs[] = {p->items_d, p->itiles_d, p->rtiles_d, p->incr_off_d, p->incr_tiles_d, p->pt_tiles_d, p->rt_tiles_d, p->group_ptr_d,
+  void* ptrs[] = {p->items_d, p->itiles_d, p->rtiles_d, p->incr_off_d, p->incr_tiles_d, p->pt_tiles_d, p->rt_tiles_d,
+                  p->fx_pt_tiles_d, p->rtt_tiles_d, p->group_ptr_d,
                   p->group_items_d, p->item_class_d, p->cls_pt_rows_d, p->cls_rt_rows_d, p->pt_row_ptr_d,
                   p->rt_row_ptr_d, p->pt_col_d, p->rt_col_d, p->pt_val_d, p->rt_val_d};
   for (void* q : ptrs) cudaFree(q);
@@ -178,7 +183,8 @@ static amr_status ensure_adjoint(amr_transfer_plan* p) {
   }
   amr_status st;
   auto drop = [&]() {
-    void** ptrs[] = {(void**)&p->pt_tiles_d, (void**)&p->rt_tiles_d, (void**)&p->group_ptr_d,
+    void** ptrs[] = {(void**)&p->pt_tiles_d, (void**)&p->rt_tiles_d, (void**)&p->fx_pt_tiles_d,
+                     (void**)&p->rtt_tiles_d, (void**)&p->group_ptr_d,
                      (void**)&p->group_items_d, (void**)&p->item_class_d, (void**)&p->cls_pt_rows_d,
                      (void**)&p->cls_rt_rows_d, (void**)&p->pt_row_ptr_d, (void**)&p->pt_col_d, (void**)&p->pt_val_d,
                      (void**)&p->rt_row_ptr_d, (void**)&p->rt_col_d, (void**)&p->rt_val_d};
@@ -195,10 +201,23 @@ static amr_status ensure_adjoint(amr_transfer_plan* p) {
       (st = upload(ab.cls_rt_rows, &p->cls_rt_rows_d)) != AMR_OK ||
       (st = upload(ab.pt.row_ptr, &p->pt_row_ptr_d)) != AMR_OK || (st = upload(ab.pt.col, &p->pt_col_d)) != AMR_OK ||
       (st = upload(ab.pt.val, &p->pt_val_d)) != AMR_OK || (st = upload(ab.rt.row_ptr, &p->rt_row_ptr_d)) != AMR_OK ||
-      (st = upload(ab.rt.col, &p->rt_col_d)) != AMR_OK || (st = upload(ab.rt.val, &p->rt_val_d)) != AMR_OK) {
+      (st = upload(ab.rt.col, &p->rt_col_d)) != AMR_OK || (st = upload(ab.rt.val, &p->rt_val_d)) != AMR_OK ||
+      (st = upload(ab.fx_pt_tiles, &p->fx_pt_tiles_d)) != AMR_OK ||
+      (st = upload(ab.rt_taylor_tiles, &p->rtt_tiles_d)) != AMR_OK) {
     drop();
     return st;
   }
+  if (ab.fx_smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute((const void*)amr::interp_adjoint_fixed_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, ab.fx_smem);
+    if (e != cudaSuccess) {
+      drop();
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    }
+  }
+  p->n_fx_pt_tiles = (int)ab.fx_pt_tiles.size();
+  p->n_rtt_tiles = (int)ab.rt_taylor_tiles.size();
+  p->fx_adj_smem = ab.fx_smem;
   p->n_pt_tiles = (int)ab.pt_tiles.size();
   p->n_rt_tiles = (int)ab.rt_tiles.size();
   p->adj_ready = true;
@@ -541,6 +560,11 @@ amr_status amr_transfer_plan_interpolate_adjoint(amr_transfer_plan* p, const dou
   if ((st = ensure_adjoint(p)) != AMR_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if (p->coarse_elems > 0) AMR_CUDA(cudaMemsetAsync(g_coarse, 0, (size_t)p->coarse_elems * 8, s));
+  if (p->n_fx_pt_tiles > 0) {
+    amr::interp_adjoint_fixed_kernel<<<p->n_fx_pt_tiles, amr::kAdjThreads, p->fx_adj_smem, s>>>(
+        p->items_d, p->fx_pt_tiles_d, p->group_ptr_d, p->group_items_d, p->U, g_fine, g_coarse);
+    AMR_CUDA(cudaGetLastError());
+  }
   if (p->n_pt_tiles > 0) {
     amr::interp_adjoint_kernel<<<p->n_pt_tiles, kThreads, 0, s>>>(
         p->items_d, p->pt_tiles_d, p->group_ptr_d, p->group_items_d, p->item_class_d, p->cls_pt_rows_d,
@@ -557,6 +581,11 @@ amr_status amr_transfer_plan_restrict_adjoint(amr_transfer_plan* p, const double
   if ((st = ensure_adjoint(p)) != AMR_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if (p->fine_elems > 0) AMR_CUDA(cudaMemsetAsync(g_fine, 0, (size_t)p->fine_elems * 8, s));
+  if (p->n_rtt_tiles > 0) {
+    amr::restrict_adjoint_taylor_kernel<<<p->n_rtt_tiles, kThreads, 0, s>>>(p->items_d, p->rtt_tiles_d, p->U,
+                                                                            g_coarse, g_fine);
+    AMR_CUDA(cudaGetLastError());
+  }
   if (p->n_rt_tiles > 0) {
     amr::restrict_adjoint_kernel<<<p->n_rt_tiles, kThreads, 0, s>>>(p->items_d, p->rt_tiles_d, p->cls_rt_rows_d,
                                                                     p->rt_row_ptr_d, p->rt_col_d, p->rt_val_d, p->U,

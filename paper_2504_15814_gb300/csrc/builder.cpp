@@ -722,15 +722,67 @@ AdjointBuild build_adjoint(const amr_transfer_desc& desc) {
     groups[x.coarse_offset].push_back((int32_t)it);
   }
   ab.group_ptr.push_back(0);
+  const int kFxSmemMax = 112 * 1024;
   for (auto& [off, members] : groups) {
     const int32_t g = (int32_t)ab.group_ptr.size() - 1;
     for (int32_t m : members) ab.group_items.push_back(m);
     ab.group_ptr.push_back((int32_t)ab.group_items.size());
-    for (int64_t u0 = 0; u0 < U; u0 += 128)
-      ab.pt_tiles.push_back({g, 0, 0, (int16_t)u0, (int16_t)std::min<int64_t>(128, U - u0)});
+    // factorised fixed-point P^T: finite differences, p a multiple of 3, and
+    // an accumulator (union of the normal stencil ranges x p x p x 32 slots)
+    // that fits the shared memory of two CTAs per SM
+    const amr_transfer_item& f = desc.items[members[0]];
+    bool fx = f.patch_size % 3 == 0;
+    int rlo = 0, rhi = -1;
+    for (int32_t m : members) {
+      const amr_transfer_item& x = desc.items[m];
+      fx = fx && x.scheme == 0;
+      IRange rn, ra, rb;
+      interp_region(x.patch_size, x.overlap, x.order, 0, x.patch_size, 0, x.patch_size, rn, ra, rb);
+      rlo = std::min(rlo, rn.lo);
+      rhi = std::max(rhi, rn.hi);
+    }
+    const int64_t smem = (int64_t)(rhi - rlo + 1) * f.patch_size * f.patch_size * 32 * 8;
+    fx = fx && smem <= kFxSmemMax && !(desc.flags & AMR_FLAG_CSR);
+    if (fx) {
+      ab.fx_smem = std::max<int>(ab.fx_smem, (int)smem);
+      const int nch = (int)((U + 31) / 32), nu = (int)((U + nch - 1) / nch);
+      for (int c = 0; c < nch; ++c)
+        ab.fx_pt_tiles.push_back({g, 0, 0, (int16_t)(c * nu), (int16_t)std::min<int64_t>(nu, U - c * nu)});
+    } else {
+      for (int64_t u0 = 0; u0 < U; u0 += 128)
+        ab.pt_tiles.push_back({g, 0, 0, (int16_t)u0, (int16_t)std::min<int64_t>(128, U - u0)});
+    }
   }
   for (int64_t it = 0; it < desc.num_items; ++it) {
-    const int nsub = desc.items[it].subface < 0 ? 9 : 1;
+    const amr_transfer_item& x = desc.items[it];
+    const int nsub = x.subface < 0 ? 9 : 1;
+    // direct R^T of Taylor items, p a multiple of 3 (each coarse halo column
+    // reaches only its own coincident fine column)
+    if (x.order >= 2 && x.patch_size % 3 == 0 && !(desc.flags & AMR_FLAG_CSR)) {
+      const int p = x.patch_size;
+      for (int sl = 0; sl < nsub; ++sl) {
+        const int sub = x.subface < 0 ? sl : x.subface;
+        int oa0, oa1, ob0, ob1;
+        owned_range(sub % 3, p, oa0, oa1);
+        owned_range(sub / 3, p, ob0, ob1);
+        for (int a0 = oa0; a0 < oa1; a0 += 12)
+          for (int b0 = ob0; b0 < ob1; b0 += 12)
+            for (int64_t u0 = 0; u0 < U; u0 += 128) {
+              Tile t{};
+              t.item = (int32_t)it;
+              t.sub = (int8_t)sub;
+              t.slot = (int8_t)(x.subface < 0 ? sl : 0);
+              t.na = (int8_t)std::min(12, oa1 - a0);
+              t.nb = (int8_t)std::min(12, ob1 - b0);
+              t.a0 = (int16_t)a0;
+              t.b0 = (int16_t)b0;
+              t.u0 = (int16_t)u0;
+              t.nu = (int16_t)std::min<int64_t>(128, U - u0);
+              ab.rt_taylor_tiles.push_back(t);
+            }
+      }
+      continue;
+    }
     for (int sl = 0; sl < nsub; ++sl)
       for (int64_t u0 = 0; u0 < U; u0 += 128)
         ab.rt_tiles.push_back({(int32_t)it, (int16_t)sl, (int16_t)ab.item_class[it], (int16_t)u0,

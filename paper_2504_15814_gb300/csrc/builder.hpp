@@ -129,7 +129,14 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget, int nu_ca
 // hanging face.
 struct AdjointBuild {
   std::vector<int32_t> group_ptr, group_items, item_class;
-  std::vector<AdjointTile> pt_tiles, rt_tiles;
+  std::vector<AdjointTile> pt_tiles, rt_tiles;  // sparse-row (CSR) work
+  // factorised work: P^T of the groups whose items all use finite
+  // differences with p a multiple of 3 (fixed-point kernel, 32-unknown
+  // chunks, fx_smem bytes of shared memory), R^T of the Taylor items with p a
+  // multiple of 3 (restriction tiles over their owned coarse columns)
+  std::vector<AdjointTile> fx_pt_tiles;
+  int fx_smem = 0;
+  std::vector<Tile> rt_taylor_tiles;
   std::vector<int32_t> cls_pt_rows, cls_rt_rows;  // offset of each class's row_ptr in the concatenation
   CsrT pt, rt;                                    // concatenated classes (row_ptr absolute into col/val)
 };

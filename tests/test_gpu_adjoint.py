@@ -33,7 +33,7 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("order,k", [(1, 1), (1, 3), (2, 2), (2, 3), (3, 2), (3, 3)])
-@pytest.mark.parametrize("precision", [B.PREC_FP64, B.PREC_SPLIT])
+@pytest.mark.parametrize("precision", [B.PREC_FP64, B.PREC_SPLIT, B.PREC_FIXED])
 def test_adjoints_match_oracle_transposes(order, k, precision):
     p, U = 6, 5
     items, cl, fl = _shared_batch(order, p, k, U)
