@@ -264,6 +264,58 @@ def interpolation_rows(face, sub, p, k, order, exact=False, scheme=SCHEME_FD):
     return outs, rows
 
 
+def diagonal_ghost_indices(face, p, k):
+    """Extended (diagonal) ghost volumes of one subface: the coarse-side
+    layers of the fine face array's index box widened tangentially by k on
+    each side, minus the ordinary ghost half -- tangential indices in
+    [-k, p + k) with at least one outside [0, p).  Returned as index triples
+    in the face array's axis order (they address positions, not storage)."""
+    n, t0, t1 = g.axes(face)
+    ghost_layers = sorted({idx[n] for idx in g.fine_ghost_indices(face, p, k)})
+    out = []
+    for i in ghost_layers:
+        for b in range(-k, p + k):
+            for a in range(-k, p + k):
+                if 0 <= a < p and 0 <= b < p:
+                    continue
+                idx = [0, 0, 0]
+                idx[n], idx[t0], idx[t1] = i, a, b
+                out.append(tuple(idx))
+    return out
+
+
+def diagonal_interpolation_rows(face, sub, p, k, order, exact=False):
+    """Rows of the diagonal-halo interpolation of subface ``sub`` (a reading:
+    the paper has no diagonal data, Sec. 2): every extended ghost volume
+    (diagonal_ghost_indices) is reconstructed from the coarse face array by
+    the same rule as the ordinary ghost volumes -- Taylor-m about the nearest
+    coarse centre of the face array (on the face's edge when the volume lies
+    past it, the offset then exceeding H/3), with that centre's stencils; or
+    the d-linear tensor product with linear extrapolation past the edge.
+    Returns (index triples, rows over the coarse face array)."""
+    num = _num(exact)
+    ext = g.extents(face, p, k)
+    coarse_idx = g.all_indices(ext)
+    coarse_x = [g.coarse_centre(face, p, k, idx) for idx in coarse_idx]
+    coarse_s = _scaled(coarse_x)
+    outs, rows = [], []
+    for fidx in diagonal_ghost_indices(face, p, k):
+        xf = g.fine_centre(face, p, k, sub, fidx)
+        if order == ORDER_DLINEAR:
+            axis_w = []
+            for d in range(3):
+                coords = sorted({x[d] for x in coarse_x})
+                axis_w.append(_bracket_weights(coords, xf[d], num))
+            row = _outer_row(ext, axis_w, num)
+        else:
+            ci = _nearest(xf, coarse_s)
+            xc = coarse_x[ci]
+            row = taylor_row(coarse_idx[ci], ext, [xf[d] - xc[d] for d in range(3)], order, num)
+        outs.append(fidx)
+        rows.append(row)
+    return outs, rows
+
+
 def restriction_rows(face, sub, p, k, order, exact=False, scheme=SCHEME_FD):
     """Rows of R for subface ``sub``: (output volumes of the coarse face array,
     rows over subface sub's fine face array).  With SCHEME_LS the fit uses the
