@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--precision", choices=["fixed", "split", "fp64"], default="fixed")
     ap.add_argument("--faces", type=int, default=N_FACES)
     ap.add_argument("--no-extra", action="store_true", help="skip the d-linear / Taylor-2 / e2e / oracle legs")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only the adjoint (P^T, R^T) of --faces hanging faces and print its JSON object")
     ap.add_argument("--tuning", default=None,
                     help="launch shape threads,smem_budget,restrict_threads,addback,lanes instead of autotuning")
     ap.add_argument("--order", type=int, default=3, choices=[1, 2, 3], help="operator order of the timed step")
@@ -309,6 +311,13 @@ def main():
     dist, rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.adjoint_only:
+        if rank == 0:
+            print(json.dumps(adjoint_leg(B, wl, torch.cuda.current_stream(dev), args.faces, max(args.steps, 1))),
+                  flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
     prec = {"fixed": B.PREC_FIXED, "split": B.PREC_SPLIT, "fp64": B.PREC_FP64}[args.precision]
     # weak scaling: a global batch of faces-per-GPU x N faces, each rank
     # keeping its cost-balanced shard (items are independent: no collective)
@@ -367,7 +376,8 @@ def main():
     restrict_gbs = info["restrict_bytes"] / (t_restrict * 1e-3) / 1e9
     ikern = {B.PREC_FIXED: "interp_fixed_kernel", B.PREC_SPLIT: "interp_kernel_split",
              B.PREC_FP64: "interp_kernel_fp64"}[prec]
-    rkern = "restrict_kernel_split" if prec == B.PREC_SPLIT else "restrict_kernel_fp64"
+    rkern = {B.PREC_FIXED: "restrict_kernel_fixed", B.PREC_SPLIT: "restrict_kernel_split",
+             B.PREC_FP64: "restrict_kernel_fp64"}[prec]
     roofline = {"bound": "hbm", "kernel": ikern, "achieved": interp_gbs, "peak": hbm_peak,
                 "unit": "GB/s", "frac": interp_gbs / hbm_peak,
                 "traffic": profiled_traffic(ikern, args.faces),
@@ -380,7 +390,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {B.PREC_FIXED: "int64 interpolation, f64 restriction", B.PREC_SPLIT: "f64 base / f32 increment",
+            "dtype": {B.PREC_FIXED: "int64", B.PREC_SPLIT: "f64 base / f32 increment",
                       B.PREC_FP64: "f64"}[prec],
             "data": "synthetic",
             "config": {"workload": f"uniform batch: {args.faces} hanging faces per GPU, p={P}, k={K}, U={U}, "
@@ -585,32 +595,7 @@ def other_workloads(B, wl, stream):
     out["puncture_split"] = res
     del items, coarse, fine, co
     torch.cuda.empty_cache()
-    # adjoint: 4,096 faces, Taylor-3, P^T and R^T; algorithmic bytes: P^T reads
-    # the ghost gradients and writes the whole coarse arrays, R^T reads the
-    # restricted halo gradients and writes the whole fine arrays (the API
-    # overwrites every gradient entry)
-    items, coarse, fine = wl.uniform_batch(n_faces=4096, U=U, order=3, config_index=4, device="cuda")
-    plan = B.Plan(items, U, coarse.numel(), fine.numel(), B.PREC_FIXED)
-    gc, gf = torch.empty_like(coarse), torch.empty_like(fine)
-    plan.interpolate_adjoint(fine, gc)  # builds the transposed tables
-    t = _time_steps(lambda: (plan.interpolate_adjoint(fine, gc), plan.restrict_adjoint(coarse, gf)), 5, stream)
-    t_pt = time_kernel(lambda: plan.interpolate_adjoint(fine, gc), 5, stream)
-    t_rt = time_kernel(lambda: plan.restrict_adjoint(coarse, gf), 5, stream)
-    nf = 4096
-    b_pt = nf * (9 * K * P * P + 2 * K * P * P) * U * 8
-    b_rt = nf * (K * P * P + 18 * K * P * P) * U * 8
-    hbm = float(measured_peaks()[0]["hbm_gbs"])
-    out["adjoint"] = {"workload": "4,096 hanging faces, p=9, k=3, U=59, Taylor-3, P^T + R^T",
-                      "ms_per_step": t, "value": (coarse.numel() + fine.numel()) / (t * 1e-3),
-                      "unit": "gradient entries/s",
-                      "interp_adjoint_ms": t_pt, "restrict_adjoint_ms": t_rt,
-                      "algorithmic_bytes": b_pt + b_rt, "achieved_gbs": (b_pt + b_rt) / (t * 1e-3) / 1e9,
-                      "frac": (b_pt + b_rt) / (t * 1e-3) / 1e9 / hbm,
-                      "interp_adjoint_gbs": b_pt / (t_pt * 1e-3) / 1e9,
-                      "restrict_adjoint_gbs": b_rt / (t_rt * 1e-3) / 1e9}
-    plan.close()
-    del items, coarse, fine, gc, gf
-    torch.cuda.empty_cache()
+    out["adjoint"] = adjoint_leg(B, wl, stream, 4096)
     return out
 
 
@@ -648,6 +633,38 @@ def compare_paths(B, wl, items, coarse, fine, coarse_out, U, args, stream, plan_
                 "err_vs_fp64": error_vs_oracle(it, coarse, fine, plan, U, n_faces=4)}
             plan.close()
     return out
+
+
+def adjoint_leg(B, wl, stream, nf, steps=5):
+    """P^T and R^T of a fixed-point Taylor-3 plan over nf hanging faces (p=9,
+    k=3, U=59).  Algorithmic bytes: P^T reads the ghost gradients and writes
+    the whole coarse arrays, R^T reads the restricted halo gradients and
+    writes the whole fine arrays (the API overwrites every gradient entry)."""
+    import torch
+    U = 59
+    items, coarse, fine = wl.uniform_batch(n_faces=nf, U=U, order=3, config_index=4, device="cuda")
+    plan = B.Plan(items, U, coarse.numel(), fine.numel(), B.PREC_FIXED)
+    gc, gf = torch.empty_like(coarse), torch.empty_like(fine)
+    plan.interpolate_adjoint(fine, gc)  # builds the transposed tables
+    t = _time_steps(lambda: (plan.interpolate_adjoint(fine, gc), plan.restrict_adjoint(coarse, gf)), steps, stream)
+    t_pt = time_kernel(lambda: plan.interpolate_adjoint(fine, gc), steps, stream)
+    t_rt = time_kernel(lambda: plan.restrict_adjoint(coarse, gf), steps, stream)
+    b_pt = nf * (9 * K * P * P + 2 * K * P * P) * U * 8
+    b_rt = nf * (K * P * P + 18 * K * P * P) * U * 8
+    hbm = float(measured_peaks()[0]["hbm_gbs"])
+    res = {"workload": f"{nf:,} hanging faces, p=9, k=3, U=59, Taylor-3, P^T + R^T",
+           "ms_per_step": t, "value": (coarse.numel() + fine.numel()) / (t * 1e-3),
+           "unit": "gradient entries/s",
+           "interp_adjoint_ms": t_pt, "restrict_adjoint_ms": t_rt,
+           "algorithmic_bytes": b_pt + b_rt, "achieved_gbs": (b_pt + b_rt) / (t * 1e-3) / 1e9,
+           "frac": (b_pt + b_rt) / (t * 1e-3) / 1e9 / hbm,
+           "interp_adjoint_gbs": b_pt / (t_pt * 1e-3) / 1e9,
+           "interp_adjoint_frac": b_pt / (t_pt * 1e-3) / 1e9 / hbm,
+           "restrict_adjoint_gbs": b_rt / (t_rt * 1e-3) / 1e9}
+    plan.close()
+    del items, coarse, fine, gc, gf
+    torch.cuda.empty_cache()
+    return res
 
 
 def e2e_leg(plan, coarse, fine, coarse_out, outs, args, stream, items=None, n_chunks=8):

@@ -106,7 +106,14 @@ typedef struct {
                             not a multiple of 3 (Sec. 5.3 notes multiples align better) a
                             subface boundary can cut a coarse volume, which the subface holding
                             3a+1 restricts (d-linear: injected along the cut axis) */
-  int32_t overlap;       /* k: 1..3; Taylor-m needs 2k >= m+1 and p >= m+1 */
+  int32_t overlap;       /* k: 1..5; Taylor-m needs 2k >= m+1 and p >= m+1.  Fine ghost layer
+                            -1-g lies inside coarse layer -1-g/3, so k = 4, 5 interpolate the
+                            ghost layers -4..-k from a second layer of coarse centres (layer
+                            -2); coarse halo layer j >= 1 is extrapolated from fine layer k-1
+                            by (3j+2-k) h (an injection where that is 0).  k = 4, 5 need p a
+                            multiple of 3 and scheme 0, no AMR_FLAG_CSR, and are served by
+                            interpolate and restrict (the adjoint and increment calls return
+                            AMR_ERR_UNSUPPORTED for such plans) */
   int32_t order;         /* amr_order */
   int32_t scheme;        /* Taylor derivative estimate: 0 tensor finite-difference stencils (default),
                             1 least-squares polynomial fit through the same centres, constrained
@@ -164,13 +171,15 @@ amr_status amr_transfer_plan_restrict(amr_transfer_plan* plan, const double* fin
  * exact integer sums; a group holding a NaN or an infinity gives NaN for that
  * unknown); the other items use explicit transposed rows in float64.  The
  * first adjoint call on a plan builds its transposed-operator tables (host
- * work and a synchronous upload): make it before capturing a stream. */
+ * work and a synchronous upload): make it before capturing a stream.
+ * AMR_ERR_UNSUPPORTED for plans with an item of overlap 4 or 5. */
 amr_status amr_transfer_plan_interpolate_adjoint(amr_transfer_plan* plan, const double* g_fine,
                                                  double* g_coarse, void* cuda_stream);
 
 /* g_fine = R^T g_coarse over the whole fine buffer: overwrites all
  * fine_elems values (zero where no weight reaches).  Only the entries of
- * g_coarse that restriction writes are read.  Float64 arithmetic. */
+ * g_coarse that restriction writes are read.  Float64 arithmetic.
+ * AMR_ERR_UNSUPPORTED for plans with an item of overlap 4 or 5. */
 amr_status amr_transfer_plan_restrict_adjoint(amr_transfer_plan* plan, const double* g_coarse,
                                               double* g_fine, void* cuda_stream);
 
@@ -185,7 +194,8 @@ amr_status amr_transfer_plan_restrict_adjoint(amr_transfer_plan* plan, const dou
  * indices q1 (t1) and q0 (t0), unknown u.  increments holds
  * amr_transfer_plan_info.increment_elems floats; d-linear items are included
  * the same way.  Works for plans of either precision; AMR_ERR_UNSUPPORTED for
- * plans with items on the sparse-row path (scheme 1 or AMR_FLAG_CSR). */
+ * plans with items on the sparse-row path (scheme 1 or AMR_FLAG_CSR) or of
+ * overlap 4 or 5. */
 amr_status amr_transfer_plan_interpolate_increments(amr_transfer_plan* plan, const double* coarse,
                                                     float* increments, void* cuda_stream);
 

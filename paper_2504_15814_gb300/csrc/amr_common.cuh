@@ -26,8 +26,8 @@ namespace amr {
 
 // One unit of device work: a rectangle of coarse columns of one subface of
 // one item, and a contiguous range of unknowns.
-//   interpolation: the coarse centres (layer -1, a, b) whose fine children
-//                  lie in the subface;
+//   interpolation: the coarse centres (a, b) of every centre layer (-1, and
+//                  -2 for overlaps 4, 5) whose fine children lie in the subface;
 //   restriction:   the coarse halo columns (a, b) over the subface.
 struct Tile {
   int32_t item;
@@ -128,16 +128,30 @@ __host__ __device__ inline IRange taylor_union(int c0, int c1, int lo, int hi, i
   return r;
 }
 
+// Deepest overlap served.  Fine ghost layer -1 - g (g = 0..k-1) lies inside
+// coarse layer -1 - g / 3, so overlaps 4 and 5 put the fine ghost layers
+// -4..-k under a second layer of interpolation centres (coarse layer -2).
+constexpr int kMaxOverlap = 5;
+// Coarse layers holding interpolation centres (layers -1, ..., -centre_layers).
+__host__ __device__ inline int centre_layers(int k) { return (k + 2) / 3; }
+// Fine ghost layers below centre layer m (coarse layer -1 - m): fine layers
+// -1 - 3m - ii for ii < child_layers(k, m).
+__host__ __device__ inline int child_layers(int k, int m) { return k - 3 * m < 3 ? k - 3 * m : 3; }
+
 // Region of the coarse face array one interpolation tile reads: signed normal
-// layers rn, tangential ranges ra (t0) and rb (t1).
+// layers rn, tangential ranges ra (t0) and rb (t1).  Each centre layer cl
+// reads layers cl and cl + 1 for d-linear (and cl - 1 when its three child
+// layers reach below it); Taylor reads the union of the derivative windows of
+// all centre layers.
 __host__ __device__ inline void interp_region(int p, int k, int order, int a0, int na, int b0, int nb,
                                               IRange& rn, IRange& ra, IRange& rb) {
+  const int cl_lo = -centre_layers(k);
   if (order == AMR_ORDER_DLINEAR) {
-    rn.lo = k >= 3 ? -2 : -1; rn.hi = 0;
+    rn.lo = child_layers(k, centre_layers(k) - 1) >= 3 ? cl_lo - 1 : cl_lo; rn.hi = 0;
     ra.lo = a0 > 0 ? a0 - 1 : 0; ra.hi = a0 + na < p ? a0 + na : p - 1;
     rb.lo = b0 > 0 ? b0 - 1 : 0; rb.hi = b0 + nb < p ? b0 + nb : p - 1;
   } else {
-    rn = taylor_union(-1, -1, -k, k - 1, order);
+    rn = taylor_union(cl_lo, -1, -k, k - 1, order);
     ra = taylor_union(a0, a0 + na - 1, 0, p - 1, order);
     rb = taylor_union(b0, b0 + nb - 1, 0, p - 1, order);
   }
@@ -157,19 +171,21 @@ constexpr int WT_SIZE = 150;
 __host__ __device__ inline int fixed_den(int L, int r) { return L == 3 ? 2 : (r == 2 ? 24 : 12); }
 
 // Least-squares line weights of the d-linear restriction, per overlap k,
-// coarse halo layer j < k and fine layer slot i < 3 (the fine patch's own
-// layers 0..k-1, or layers -1, 0 when k = 1).
-constexpr int LS_SIZE = 3 * 3 * 3;
-__host__ __device__ inline int ls_index(int k, int j, int i) { return ((k - 1) * 3 + j) * 3 + i; }
+// coarse halo layer j < k and fine layer slot i < kMaxOverlap (the fine
+// patch's own layers 0..k-1, or layers -1, 0 when k = 1).
+constexpr int LS_SIZE = kMaxOverlap * kMaxOverlap * kMaxOverlap;
+__host__ __device__ inline int ls_index(int k, int j, int i) {
+  return ((k - 1) * kMaxOverlap + j) * kMaxOverlap + i;
+}
 
 // Combined Taylor restriction weights: coarse halo layer j >= 1 of a face with
-// overlap k (2 or 3) and order m (2 or 3) is sum_i W[i] u(fine layer s + i)
-// over the derivative window (s, L) about fine layer k - 1 (Sec. 3: Taylor
-// about the nearest fine cell, extrapolated by (3j + 2 - k) h), for the
-// finite-difference (scheme 0) or least-squares (scheme 1) derivatives.
-constexpr int RW_SIZE = 16 * 5;
+// overlap k (2..kMaxOverlap) and order m (2 or 3) is sum_i W[i] u(fine layer
+// s + i) over the derivative window (s, L) about fine layer k - 1 (Sec. 3:
+// Taylor about the nearest fine cell, extrapolated by (3j + 2 - k) h), for
+// the finite-difference (scheme 0) or least-squares (scheme 1) derivatives.
+constexpr int RW_SIZE = 2 * 2 * (kMaxOverlap - 1) * (kMaxOverlap - 1) * 5;
 __host__ __device__ inline int rw_index(int order, int k, int j, int scheme = 0) {
-  return ((((scheme * 2 + order - 2) * 2 + (k - 2)) * 2) + (j - 1)) * 5;
+  return ((((scheme * 2 + order - 2) * (kMaxOverlap - 1) + (k - 2)) * (kMaxOverlap - 1)) + (j - 1)) * 5;
 }
 
 // Least-squares interpolation (scheme 1) in the factorised kernel: the

@@ -52,6 +52,8 @@ amr_status upload_tables(int device) {
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw_hi, t.rw_hi, sizeof t.rw_hi));
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw_lo, t.rw_lo, sizeof t.rw_lo));
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_fxw, t.fxw, sizeof t.fxw));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_rwx, t.rwx, sizeof t.rwx));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw_den, t.rw_den, sizeof t.rw_den));
   g_tables_ready[device] = 1;
   return AMR_OK;
 }
@@ -168,8 +170,17 @@ static void free_plan(amr_transfer_plan* p) {
 }
 
 // Build and upload the transposed operators (synchronous; first adjoint call).
+// Items with overlap 4 or 5 (two layers of interpolation centres) are served
+// by interpolate and restrict only.
+static bool has_deep_overlap(const amr_transfer_plan* p) {
+  for (const amr_transfer_item& x : p->items_h)
+    if (x.overlap > 3) return true;
+  return false;
+}
+
 static amr_status ensure_adjoint(amr_transfer_plan* p) {
   if (p->adj_ready) return AMR_OK;
+  if (has_deep_overlap(p)) return AMR_ERR_UNSUPPORTED;  // adjoints serve overlaps 1..3
   amr_transfer_desc d{};
   d.abi_version = AMR_TRANSFER_ABI_VERSION;
   d.num_unknowns = p->U;
@@ -499,6 +510,7 @@ amr_status amr_transfer_plan_interpolate_increments(amr_transfer_plan* p, const 
   amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, increments, p ? (p->info.increment_elems + 1) / 2 : 0);
   if (st != AMR_OK) return st;
   if (p->n_cpt > 0 || p->n_crt > 0) return AMR_ERR_UNSUPPORTED;  // increments come from the factorised kernel
+  if (has_deep_overlap(p)) return AMR_ERR_UNSUPPORTED;            // increments serve overlaps 1..3
   if (p->n_iseg[2] > 0 || p->n_iseg[3] > 0) return AMR_ERR_UNSUPPORTED;  // finite-difference items only
   if (p->n_iseg[0] > 0) {
     amr::interp_kernel<true, 0, true><<<p->n_iseg[0], p->tuning.interp_threads, p->interp_smem, (cudaStream_t)stream>>>(
@@ -525,6 +537,7 @@ amr_status amr_transfer_plan_apply_increments(amr_transfer_plan* p, const double
                      ranges_overlap(increments, ibytes, coarse, p->coarse_elems * 8)))
     return AMR_ERR_INVALID_ARGUMENT;
   if (p->n_cpt > 0 || p->n_crt > 0) return AMR_ERR_UNSUPPORTED;
+  if (has_deep_overlap(p)) return AMR_ERR_UNSUPPORTED;
   if (p->n_incr_tiles == 0) return AMR_OK;
   amr::apply_increments_kernel<<<p->n_incr_tiles, kThreads, 0, (cudaStream_t)stream>>>(
       p->items_d, p->incr_tiles_d, p->incr_off_d, p->U, coarse, increments, fine);
@@ -545,6 +558,9 @@ amr_status amr_transfer_plan_restrict(amr_transfer_plan* p, const double* fine, 
   if (p->n_rtiles == 0) return AMR_OK;
   if (p->precision == AMR_PREC_SPLIT)
     amr::restrict_kernel<amr::kRestrictSplit><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(
+        p->items_d, p->rtiles_d, p->U, fine, coarse);
+  else if (p->precision == AMR_PREC_FIXED)
+    amr::restrict_kernel<amr::kRestrictFixed><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(
         p->items_d, p->rtiles_d, p->U, fine, coarse);
   else
     amr::restrict_kernel<amr::kRestrictF64><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(

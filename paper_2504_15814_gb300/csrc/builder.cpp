@@ -82,7 +82,7 @@ Tables make_tables() {
       }
   // Least-squares line through the fine patch's own layers (centres at
   // (i + 1/2)/3 H), evaluated at coarse halo layer j (centre (j + 1/2) H).
-  for (int k = 1; k <= 3; ++k) {
+  for (int k = 1; k <= kMaxOverlap; ++k) {
     std::vector<int> layers;
     if (k == 1) layers = {-1, 0};
     else for (int i = 0; i < k; ++i) layers.push_back(i);
@@ -105,12 +105,13 @@ Tables make_tables() {
   // sum_r coeff_r(i) e^r with coeff_r the Taylor coefficient weights about
   // fine layer k - 1 on the window (s, L) and e = 3j + 2 - k.
   for (int order = 2; order <= 3; ++order)
-    for (int k = 2; k <= 3; ++k)
+    for (int k = 2; k <= kMaxOverlap; ++k)
       for (int j = 1; j < k; ++j) {
         int s0, L;
         stencil_window(k - 1, -k, k - 1, pure_exactness(order), s0, L);
         const int pos = k - 1 - s0;
         const int e = 3 * j + 2 - k;
+        Q row[5];
         for (int i = 0; i < 5; ++i) {
           Q w(0);
           if (i < L) {
@@ -125,7 +126,29 @@ Tables make_tables() {
           t.rw[idx] = w.to_double();
           t.rw_hi[idx] = (float)t.rw[idx];
           t.rw_lo[idx] = (float)(t.rw[idx] - (double)t.rw_hi[idx]);
+          row[i] = w;
         }
+        // exact integer form: D = lcm of the row's denominators = 2^a 3^b
+        int64_t D = 1;
+        for (int i = 0; i < 5; ++i) D = std::lcm(D, row[i].d);
+        int a2 = 0, b3 = 0;
+        int64_t rest = D;
+        while (rest % 2 == 0) { rest /= 2; ++a2; }
+        while (rest % 3 == 0) { rest /= 3; ++b3; }
+        if (rest != 1 || b3 > 1 || a2 > 15) {
+          std::fprintf(stderr, "amr_transfer: restriction weight denominator %lld (order %d, k %d, j %d)\n",
+                       (long long)D, order, k, j);
+          std::abort();
+        }
+        for (int i = 0; i < 5; ++i) {
+          const Q n = row[i] * Q(D);
+          if (n.d != 1 || n.n > (1 << 20) || n.n < -(1 << 20)) {
+            std::fprintf(stderr, "amr_transfer: restriction numerator out of range (order %d, k %d, j %d)\n", order, k, j);
+            std::abort();
+          }
+          t.rwx[rw_index(order, k, j) + i] = (int32_t)n.n;
+        }
+        t.rw_den[rw_index(order, k, j) / 5] = a2 | b3 << 4;
         // least-squares scheme: the fit along the same window through the
         // expansion value (the base takes 1 - sum of the others)
         std::vector<std::array<int, 3>> rel;
@@ -146,22 +169,22 @@ Tables make_tables() {
   return t;
 }
 
-// Mark the volumes one interpolation centre references; reference volume index
-// (j + k) * p * p + b * p + a.
-void mark_interp(std::vector<char>& m, int p, int k, int order, int a, int b) {
+// Mark the volumes one interpolation centre (cl, a, b) references (kk child
+// layers below it); reference volume index (j + k) * p * p + b * p + a.
+void mark_interp_layer(std::vector<char>& m, int p, int k, int order, int cl, int kk, int a, int b) {
   auto mark = [&](int j, int aa, int bb) { m[((size_t)(j + k) * p + bb) * p + aa] = 1; };
   if (order == AMR_ORDER_DLINEAR) {
-    const int jlo = k >= 3 ? -2 : -1;
+    const int jlo = kk >= 3 ? cl - 1 : cl;
     const int alo = (a == 0) ? 0 : a - 1, ahi = (a == p - 1) ? p - 1 : a + 1;
     const int blo = (b == 0) ? 0 : b - 1, bhi = (b == p - 1) ? p - 1 : b + 1;
-    for (int j = jlo; j <= 0; ++j) {
+    for (int j = jlo; j <= cl + 1; ++j) {
       for (int bb = blo; bb <= bhi; ++bb)
         for (int aa = alo; aa <= ahi; ++aa) mark(j, aa, bb);
     }
     return;
   }
   int s, l;
-  const int c[3] = {-1, a, b};
+  const int c[3] = {cl, a, b};
   const int lo[3] = {-k, 0, 0}, hi[3] = {k - 1, p - 1, p - 1};
   for (int d = 0; d < 3; ++d) {  // pure derivatives: lines through the centre
     stencil_window(c[d], lo[d], hi[d], pure_exactness(order), s, l);
@@ -186,6 +209,11 @@ void mark_interp(std::vector<char>& m, int p, int k, int order, int a, int b) {
     for (int q0 = ms[0]; q0 < ms[0] + ml[0]; ++q0)
       for (int q1 = ms[1]; q1 < ms[1] + ml[1]; ++q1)
         for (int q2 = ms[2]; q2 < ms[2] + ml[2]; ++q2) mark(q0, q1, q2);
+}
+
+// Every centre layer of tangential position (a, b).
+void mark_interp(std::vector<char>& m, int p, int k, int order, int a, int b) {
+  for (int ml = 0; ml < centre_layers(k); ++ml) mark_interp_layer(m, p, k, order, -1 - ml, child_layers(k, ml), a, b);
 }
 
 // Fine volumes one restriction column references (reference frame of the
@@ -260,7 +288,9 @@ BuildResult build_plan(const amr_transfer_desc& desc, int smem_budget, int nu_ca
     if (x.patch_size < 1 || x.overlap < 1) return bad(AMR_ERR_INVALID_ARGUMENT, "p and k must be positive");
     if (x.overlap > x.patch_size) return bad(AMR_ERR_INVALID_ARGUMENT, "k > p");
     if (x.patch_size > 48) return bad(AMR_ERR_UNSUPPORTED, "p > 48");
-    if (x.overlap > 3) return bad(AMR_ERR_UNSUPPORTED, "k > 3");
+    if (x.overlap > kMaxOverlap) return bad(AMR_ERR_UNSUPPORTED, "k > 5");
+    if (x.overlap > 3 && (x.patch_size % 3 != 0 || x.scheme != 0 || (desc.flags & AMR_FLAG_CSR)))
+      return bad(AMR_ERR_UNSUPPORTED, "k > 3 needs p a multiple of 3, finite-difference derivatives, no CSR flag");
     if (x.order >= 2 && (2 * x.overlap < x.order + 1 || x.patch_size < x.order + 1))
       return bad(AMR_ERR_UNSUPPORTED, "Taylor order needs 2k >= m+1 and p >= m+1");
     if (x.coarse_offset < 0 || x.fine_offset < 0) return bad(AMR_ERR_INVALID_ARGUMENT, "negative offset");

@@ -125,14 +125,15 @@ __device__ __forceinline__ void fx_pure5(const Y& y, int pp, long long& r1, long
 }
 
 // ---------------------------------------------------------------------------
-// Taylor-m (m = 2, 3) interpolation of one coarse centre (layer -1, a, b) and
+// Taylor-m (m = 2, 3) interpolation of one coarse centre (layer cl, a, b) and
 // one unknown in exact integers.  D(j, a', b') returns n(j, a', b') - n_c.
-// emit(ii, e0, e1, S) receives S = G (child - centre) / q for the child in
-// fine signed layer -1-ii and tangential offsets e0, e1 (as taylor_interp_core).
+// emit(ii, e0, e1, S) receives S = G (child - centre) / q for the child ii < kk
+// below the centre and tangential offsets e0, e1 (as taylor_interp_core).
 // ---------------------------------------------------------------------------
 template <int M, typename Diff, typename Emit>
-__device__ __forceinline__ void taylor_fixed_core(const Diff& D, const Emit& emit, int k, int p, int a, int b) {
-  const int c[3] = {-1, a, b};
+__device__ __forceinline__ void taylor_fixed_core(const Diff& D, const Emit& emit, int k, int p, int a, int b,
+                                                  int cl = -1, int kk = 3) {
+  const int c[3] = {cl, a, b};
   const int lo[3] = {-k, 0, 0};
   const int hi[3] = {k - 1, p - 1, p - 1};
   int ps[3], pl[3], ms[3], ml[3];
@@ -204,7 +205,7 @@ __device__ __forceinline__ void taylor_fixed_core(const Diff& D, const Emit& emi
   }
 
   // Mixed derivatives from the 3x3x3 box of the 3-point windows (normal
-  // window always centred on layer -1), collapsed along the normal, then t0,
+  // window always centred on the centre's layer), collapsed along the normal, then t0,
   // then t1, each box value read once; numerators over 2 per differentiated
   // axis.  Taylor-2 needs only the three planes through the centre.
   {
@@ -255,14 +256,16 @@ __device__ __forceinline__ void taylor_fixed_core(const Diff& D, const Emit& emi
       C[1][1][0] = m110; C[1][0][1] = m101; C[0][1][1] = m011;
     }
   }
-  taylor_children<M, long long>(C, emit, k);
+  taylor_children<M, long long>(C, emit, kk < k ? kk : k);
 }
 
 // d-linear interpolation of one coarse centre in exact integers (G = 27:
 // each 1-D lerp has weights in thirds).  D and emit as above (the centre's
 // own difference is 0).
 template <typename Diff, typename Emit>
-__device__ __forceinline__ void dlinear_fixed_core(const Diff& D, const Emit& emit, int k, int p, int a, int b) {
+__device__ __forceinline__ void dlinear_fixed_core(const Diff& D, const Emit& emit, int k, int p, int a, int b,
+                                                   int cl = -1, int kk = 3) {
+  if (kk > k) kk = k;
   const bool alo = a == 0, ahi = a == p - 1, blo = b == 0, bhi = b == p - 1;
   const int aidx[3] = {alo ? a : a - 1, a, ahi ? a : a + 1};
   const int bidx[3] = {blo ? b : b - 1, b, bhi ? b : b + 1};
@@ -271,12 +274,12 @@ __device__ __forceinline__ void dlinear_fixed_core(const Diff& D, const Emit& em
   for (int da = 0; da < 3; ++da)
 #pragma unroll
     for (int db = 0; db < 3; ++db) {
-      const long long v1 = D(-1, aidx[da], bidx[db]);
-      const long long v0 = D(0, aidx[da], bidx[db]);
-      N[0][da][db] = 2 * v1 + v0;  // fine layer -1: v1 + (v0 - v1) / 3
-      N[1][da][db] = 3 * v1;       // fine layer -2: coincident with coarse layer -1
+      const long long v1 = D(cl, aidx[da], bidx[db]);
+      const long long v0 = D(cl + 1, aidx[da], bidx[db]);
+      N[0][da][db] = 2 * v1 + v0;  // child above: v1 + (v0 - v1) / 3
+      N[1][da][db] = 3 * v1;       // child coincident with coarse layer cl
       N[2][da][db] = 3 * v1;
-      if (k >= 3) N[2][da][db] = 2 * v1 + D(-2, aidx[da], bidx[db]);  // fine layer -3
+      if (kk >= 3) N[2][da][db] = 2 * v1 + D(cl - 1, aidx[da], bidx[db]);  // child below
     }
   // 3 x the 1-D lerp to offsets -1, 0, +1 (linear extrapolation at an edge)
   auto lerp3 = [](long long xm, long long x0, long long xp, bool le, bool he, long long& rm, long long& rz,
@@ -287,7 +290,7 @@ __device__ __forceinline__ void dlinear_fixed_core(const Diff& D, const Emit& em
   };
 #pragma unroll
   for (int ii = 0; ii < 3; ++ii) {
-    if (ii >= k) break;
+    if (ii >= kk) break;
     long long Am[3], Az[3], Ap[3];
 #pragma unroll
     for (int db = 0; db < 3; ++db) lerp3(N[ii][0][db], N[ii][1][db], N[ii][2][db], alo, ahi, Am[db], Az[db], Ap[db]);
@@ -395,11 +398,12 @@ __global__ void __launch_bounds__(kMaxFixedThreads, 2)
   // neighbours along t0 are compile-time offsets
   constexpr int SA = 32;
   const int SB = NA * 32, SJ = NB * NA * 32;
-  const int ntask = t.na * t.nb;
+  const int ntask = t.na * t.nb * centre_layers(k);  // centres (a, b) of each centre layer
   Counter4 c;
   c.init(warp, nw, 1, t.na, t.nb);
   for (int e = lane < nu ? warp : ntask; e < ntask; e += nw, c.advance(1, t.na, t.nb)) {
     const int u = lane, a = t.a0 + c.x, b = t.b0 + c.y;
+    const int cl = -1 - c.z, kk = child_layers(k, c.z);  // centre layer and its child layers
     ChildMap cm;
     CutAxis ca, cbx;
     if constexpr (CUT) {
@@ -418,13 +422,13 @@ __global__ void __launch_bounds__(kMaxFixedThreads, 2)
       cm = child_map(t, p, a, b);
     }
     double* fc = fine + it.fine_offset + (int64_t)cm.slot * arr +
-                 frame_vol(fr, -1, 3 * a + cm.q0_off, 3 * b + cm.q1_off) * U + t.u0 + u;
-    const int ic = (((-1 - rn.lo) * NB + (b - rb.lo)) * NA + (a - ra.lo)) * 32 + u;
+                 frame_vol(fr, cl - 2 * c.z, 3 * a + cm.q0_off, 3 * b + cm.q1_off) * U + t.u0 + u;
+    const int ic = (((cl - rn.lo) * NB + (b - rb.lo)) * NA + (a - ra.lo)) * 32 + u;
     const long long nc = sm[ic];
     const long long Gnc = (long long)fs.G * nc;
-    const double base = __ldg(cb + frame_vol(fr, -1, a, b) * U + u);
+    const double base = __ldg(cb + frame_vol(fr, cl, a, b) * U + u);
     auto D = [&](int j, int aa, int bb) -> long long {
-      return sm[ic + (j + 1) * SJ + (bb - b) * SB + (aa - a) * SA] - nc;
+      return sm[ic + (j - cl) * SJ + (bb - b) * SB + (aa - a) * SA] - nc;
     };
     auto emit = [&](int ii, int e0, int e1, long long S) {
       double v;
@@ -438,9 +442,9 @@ __global__ void __launch_bounds__(kMaxFixedThreads, 2)
         fc[-ii * gs_n + e0 * gs_a + e1 * gs_b] = v;
       }
     };
-    if (m == 3) taylor_fixed_core<3>(D, emit, k, p, a, b);
-    else if (m == 2) taylor_fixed_core<2>(D, emit, k, p, a, b);
-    else dlinear_fixed_core(D, emit, k, p, a, b);
+    if (m == 3) taylor_fixed_core<3>(D, emit, k, p, a, b, cl, kk);
+    else if (m == 2) taylor_fixed_core<2>(D, emit, k, p, a, b, cl, kk);
+    else dlinear_fixed_core(D, emit, k, p, a, b, cl, kk);
   }
 }
 

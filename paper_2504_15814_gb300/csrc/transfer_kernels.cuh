@@ -36,6 +36,8 @@ __constant__ float c_ls_f[LS_SIZE];
 __constant__ double c_rw[RW_SIZE];
 __constant__ float c_rw_hi[RW_SIZE];
 __constant__ float c_rw_lo[RW_SIZE];
+__constant__ int32_t c_rwx[RW_SIZE];       // integer restriction weights (Tables::rwx)
+__constant__ int32_t c_rw_den[RW_SIZE / 5];  // their row denominators 2^a 3^b as a | b << 4
 
 template <bool SPLIT> struct Arith;
 template <> struct Arith<false> {
@@ -111,17 +113,19 @@ __device__ __forceinline__ void taylor_children(const T (&C)[M + 1][M + 1][M + 1
 
 
 // ---------------------------------------------------------------------------
-// Taylor-m interpolation of one coarse centre (layer -1, a, b) and one
+// Taylor-m interpolation of one coarse centre (layer cl, a, b) and one
 // unknown.  D(j, a', b') returns the input value (float64 path) or its
 // difference to the centre value (split path); c000 is the centre value or 0.
-// emit(ii, e0, e1, v) receives the Taylor value (or increment) of the child in
-// fine signed layer -1-ii (normal offset +1, 0, -1 for ii = 0, 1, 2, units of
-// h) and tangential offsets e0, e1 in {-1, 0, 1}.
+// emit(ii, e0, e1, v) receives the Taylor value (or increment) of the child
+// ii < kk below the centre (normal offset +1, 0, -1 for ii = 0, 1, 2, units
+// of h; fine signed layer -1-ii for cl = -1) and tangential offsets e0, e1 in
+// {-1, 0, 1}.
 // ---------------------------------------------------------------------------
 template <int M, typename T, typename Diff, typename Emit>
 __device__ __forceinline__ void taylor_interp_core(const Diff& D, const Emit& emit, const T* __restrict__ wt,
-                                                   int k, int p, int a, int b, T c000) {
-  const int c[3] = {-1, a, b};
+                                                   int k, int p, int a, int b, T c000, int cl = -1,
+                                                   int kk = 3) {
+  const int c[3] = {cl, a, b};
   const int lo[3] = {-k, 0, 0};
   const int hi[3] = {k - 1, p - 1, p - 1};
   int ps[3], pl[3], ms[3], ml[3];
@@ -168,7 +172,8 @@ __device__ __forceinline__ void taylor_interp_core(const Diff& D, const Emit& em
   // Mixed derivatives.  Every axis's mixed window has 3 points (ms[d] ..
   // ms[d] + 2) for Taylor orders, so all of them come from one 3x3x3 box of
   // values, collapsed axis by axis: along the normal into (value at c, r = 1,
-  // r = 2) -- the normal window is centred on layer -1, as 2k >= m + 1 >= 3 --
+  // r = 2) -- the normal window is centred on the centre's layer, as
+  // 2k >= m + 1 >= 3 and a second centre layer exists only for k >= 4 --
   // then along t0 into (value at c, r = 1, r = 2) with c's box index sa, then
   // along t1 likewise.  Each box value is read once.
   {
@@ -231,7 +236,7 @@ __device__ __forceinline__ void taylor_interp_core(const Diff& D, const Emit& em
     }
   }
 
-  taylor_children<M, T>(C, emit, k);
+  taylor_children<M, T>(C, emit, kk < k ? kk : k);
 }
 
 // Least-squares Taylor-m interpolation of one coarse centre (scheme 1; the
@@ -320,7 +325,9 @@ __device__ __forceinline__ Tri<T> dlin3(T xm, T x0, T xp, bool lo_edge, bool hi_
 // neighbour columns, then along t0, then along t1 (the tensor product
 // P = P_t1 P_t0 P_n of Sec. 2, sum-factorised).  Same D / emit contract.
 template <typename T, typename Diff, typename Emit>
-__device__ __forceinline__ void dlinear_interp_core(const Diff& D, const Emit& emit, int k, int p, int a, int b) {
+__device__ __forceinline__ void dlinear_interp_core(const Diff& D, const Emit& emit, int k, int p, int a, int b,
+                                                    int cl = -1, int kk = 3) {
+  if (kk > k) kk = k;
   const bool alo = a == 0, ahi = a == p - 1, blo = b == 0, bhi = b == p - 1;
   const int aidx[3] = {alo ? a : a - 1, a, ahi ? a : a + 1};
   const int bidx[3] = {blo ? b : b - 1, b, bhi ? b : b + 1};
@@ -330,16 +337,16 @@ __device__ __forceinline__ void dlinear_interp_core(const Diff& D, const Emit& e
   for (int da = 0; da < 3; ++da)
 #pragma unroll
     for (int db = 0; db < 3; ++db) {
-      const T v1 = D(-1, aidx[da], bidx[db]);
-      const T v0 = D(0, aidx[da], bidx[db]);
-      N[0][da][db] = v1 + third * (v0 - v1);  // fine layer -1: towards coarse layer 0
-      N[1][da][db] = v1;                      // fine layer -2: coincident with coarse layer -1
+      const T v1 = D(cl, aidx[da], bidx[db]);
+      const T v0 = D(cl + 1, aidx[da], bidx[db]);
+      N[0][da][db] = v1 + third * (v0 - v1);  // child above the centre: towards coarse layer cl + 1
+      N[1][da][db] = v1;                      // child coincident with coarse layer cl
       N[2][da][db] = v1;
-      if (k >= 3) N[2][da][db] = v1 + third * (D(-2, aidx[da], bidx[db]) - v1);  // fine layer -3
+      if (kk >= 3) N[2][da][db] = v1 + third * (D(cl - 1, aidx[da], bidx[db]) - v1);  // child below
     }
 #pragma unroll
   for (int ii = 0; ii < 3; ++ii) {
-    if (ii >= k) break;
+    if (ii >= kk) break;
     Tri<T> A[3];
 #pragma unroll
     for (int db = 0; db < 3; ++db) A[db] = dlin3<T>(N[ii][0][db], N[ii][1][db], N[ii][2][db], alo, ahi);
@@ -497,11 +504,12 @@ __global__ void __launch_bounds__(SPLIT ? kMaxSplitInterpThreads : 256, 2)
   const int w_nu = per_warp ? 1 : nu;
   const int e_first = per_warp ? (int)(threadIdx.x >> 5) : (int)threadIdx.x;
   const int e_step = per_warp ? (int)(blockDim.x >> 5) : (int)blockDim.x;
-  const int ntask = t.na * t.nb * w_nu;
+  const int ntask = t.na * t.nb * w_nu * centre_layers(k);  // centres (a, b) of each centre layer
   Counter4 c;
   c.init(e_first, e_step, w_nu, t.na, t.nb);
   for (int e = (per_warp && lane >= nu) ? ntask : e_first; e < ntask; e += e_step, c.advance(w_nu, t.na, t.nb)) {
     const int u = per_warp ? lane : c.u, a = t.a0 + c.x, b = t.b0 + c.y;
+    const int cl = -1 - c.z, kk = child_layers(k, c.z);  // centre layer and its child layers
     ChildMap cm;
     CutAxis ca, cbx;
     if constexpr (CUT) {
@@ -523,11 +531,11 @@ __global__ void __launch_bounds__(SPLIT ? kMaxSplitInterpThreads : 256, 2)
     } else {
       cm = child_map(t, p, a, b);
     }
-    // child (fine layer -1, tangential offsets 0, 0) of this centre and unknown
+    // child ii = 0 (fine layer -1 - 3 c.z, tangential offsets 0, 0) of this centre and unknown
     double* fc = fine + it.fine_offset + (int64_t)cm.slot * arr +
-                 frame_vol(fr, -1, 3 * a + cm.q0_off, 3 * b + cm.q1_off) * U + t.u0 + u;
-    const int ic = ((-1 - rn.lo) * NB + (b - rb.lo)) * NA * nu + (a - ra.lo) * nu + u;
-    auto S = [&](int j, int aa, int bb) -> SType { return sm[ic + (j + 1) * SJ + (bb - b) * SB + (aa - a) * SA]; };
+                 frame_vol(fr, cl - 2 * c.z, 3 * a + cm.q0_off, 3 * b + cm.q1_off) * U + t.u0 + u;
+    const int ic = ((cl - rn.lo) * NB + (b - rb.lo)) * NA * nu + (a - ra.lo) * nu + u;
+    auto S = [&](int j, int aa, int bb) -> SType { return sm[ic + (j - cl) * SJ + (bb - b) * SB + (aa - a) * SA]; };
     auto store = [&](int ii, int e0, int e1, double v) {
       if constexpr (CUT) {
         if (cut_valid(ca, e0) && cut_valid(cbx, e1)) fc[-ii * gs_n + cut_off(ca, e0) + cut_off(cbx, e1)] = v;
@@ -537,7 +545,7 @@ __global__ void __launch_bounds__(SPLIT ? kMaxSplitInterpThreads : 256, 2)
     };
     if constexpr (SPLIT) {
       const F2 hc = sm[ic];
-      const double base = __ldg(cb + frame_vol(fr, -1, a, b) * U + u);
+      const double base = __ldg(cb + frame_vol(fr, cl, a, b) * U + u);
       auto D = [&](int j, int aa, int bb) -> float {
         const F2 x = S(j, aa, bb);
         return __fadd_rn(__fsub_rn(x.hi, hc.hi), __fsub_rn(x.lo, hc.lo));
@@ -574,9 +582,9 @@ __global__ void __launch_bounds__(SPLIT ? kMaxSplitInterpThreads : 256, 2)
         if (m == 3) ls_interp_core<3, false, float>(D, emit, wc, ws, k, p, a, b, 0.f);
         else ls_interp_core<2, false, float>(D, emit, wc, ws, k, p, a, b, 0.f);
       } else {
-        if (m == 3) taylor_interp_core<3, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
-        else if (m == 2) taylor_interp_core<2, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f);
-        else dlinear_interp_core<float>(D, emit, k, p, a, b);
+        if (m == 3) taylor_interp_core<3, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f, cl, kk);
+        else if (m == 2) taylor_interp_core<2, float>(D, emit, c_wt_interp_f, k, p, a, b, 0.f, cl, kk);
+        else dlinear_interp_core<float>(D, emit, k, p, a, b, cl, kk);
       }
     } else {
       auto emit = [&](int ii, int e0, int e1, double v) { store(ii, e0, e1, v); };
@@ -588,9 +596,9 @@ __global__ void __launch_bounds__(SPLIT ? kMaxSplitInterpThreads : 256, 2)
         if (m == 3) ls_interp_core<3, true, double>(S, emit, wc, ws, k, p, a, b, S(-1, a, b));
         else ls_interp_core<2, true, double>(S, emit, wc, ws, k, p, a, b, S(-1, a, b));
       } else {
-        if (m == 3) taylor_interp_core<3, double>(S, emit, c_wt_interp, k, p, a, b, S(-1, a, b));
-        else if (m == 2) taylor_interp_core<2, double>(S, emit, c_wt_interp, k, p, a, b, S(-1, a, b));
-        else dlinear_interp_core<double>(S, emit, k, p, a, b);
+        if (m == 3) taylor_interp_core<3, double>(S, emit, c_wt_interp, k, p, a, b, S(cl, a, b), cl, kk);
+        else if (m == 2) taylor_interp_core<2, double>(S, emit, c_wt_interp, k, p, a, b, S(cl, a, b), cl, kk);
+        else dlinear_interp_core<double>(S, emit, k, p, a, b, cl, kk);
       }
     }
   }
@@ -656,7 +664,7 @@ __device__ __forceinline__ double pick5(const double* v, int idx) {
 // weighted sum; each output rebuilt as float64 without float64 instructions.
 template <typename Store>
 __device__ __forceinline__ void taylor_extrapolate_split(const double* v, int L, int pos, int m, int k, int j0,
-                                                         int scheme, const Store& store) {
+                                                         int j1, int scheme, const Store& store) {
   const F2 b = split_f64(pick5(v, pos));
   float dh[5], dl[5];
 #pragma unroll
@@ -670,7 +678,7 @@ __device__ __forceinline__ void taylor_extrapolate_split(const double* v, int L,
       dl[i] = __fadd_rn(e, __fsub_rn(x.lo, b.lo));
     }
   }
-  for (int j = j0; j < k; ++j) {
+  for (int j = j0; j < k && j < j1; ++j) {
     const int w0 = rw_index(m, k, j, scheme);
     float ah = 0.f, al = 0.f;
 #pragma unroll
@@ -697,9 +705,9 @@ __device__ __forceinline__ void taylor_extrapolate_split(const double* v, int L,
 template <typename Fine, typename Coarse>
 __device__ __forceinline__ void dlinear_restrict_f64(const Fine& F, const Coarse& C, int k) {
   const int nl = k == 1 ? 2 : k;
-  double avg[3] = {0.0, 0.0, 0.0};
+  double avg[kMaxOverlap] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-  for (int sl = 0; sl < 3; ++sl) {
+  for (int sl = 0; sl < kMaxOverlap; ++sl) {
     if (sl < nl) {
       double v[9];  // one fine layer: all 9 loads before the sum
 #pragma unroll
@@ -713,7 +721,7 @@ __device__ __forceinline__ void dlinear_restrict_f64(const Fine& F, const Coarse
   for (int j = 0; j < k; ++j) {
     double r = 0.0;
 #pragma unroll
-    for (int sl = 0; sl < 3; ++sl)
+    for (int sl = 0; sl < kMaxOverlap; ++sl)
       if (sl < nl) r += c_ls[ls_index(k, j, sl)] * avg[sl];
     C(j, r);
   }
@@ -725,9 +733,9 @@ template <typename Fine, typename Coarse>
 __device__ __forceinline__ void dlinear_restrict_split(const Fine& F, const Coarse& C, int k) {
   const int nl = k == 1 ? 2 : k;
   const F2 r = split_f64(F(0, 0, 0));  // fine layer 0, centre column
-  float avg[3] = {0.f, 0.f, 0.f};
+  float avg[kMaxOverlap] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int sl = 0; sl < 3; ++sl) {
+  for (int sl = 0; sl < kMaxOverlap; ++sl) {
     if (sl < nl) {
       double v[9];  // one fine layer: all 9 loads before the arithmetic
 #pragma unroll
@@ -744,16 +752,97 @@ __device__ __forceinline__ void dlinear_restrict_split(const Fine& F, const Coar
   for (int j = 0; j < k; ++j) {
     float w = 0.f;
 #pragma unroll
-    for (int sl = 0; sl < 3; ++sl)
+    for (int sl = 0; sl < kMaxOverlap; ++sl)
       if (sl < nl) w += c_ls_f[ls_index(k, j, sl)] * avg[sl];
     C(j, add_back(r, w));
   }
 }
 
-// Restriction precision modes: float64 throughout (float64 and fixed-point
-// plans), or split (float64 first extrapolated layer, float-pair deeper
-// layers, float32 d-linear averaging on exact float-pair differences).
-constexpr int kRestrictF64 = 0, kRestrictSplit = 1;
+// ---------------------------------------------------------------------------
+// Exact Taylor restriction of one column (fixed-point plans).  The window
+// values v[0..L) are rounded once onto the grid 2^-s with s = 1084 - E (E the
+// largest biased exponent of the window), |n| < 2^62, so the rounding error
+// is at most 2^-62 of the window's largest magnitude; each n is carried as
+// two signed 31-bit halves, so the weighted sums over the integer weights
+// (|W| < 2^15) are exact in two int64 accumulators, A (high halves) and B.
+// The result T 2^-s / D, T = A 2^31 + B, is normalised from 128 bits with
+// one round-to-nearest-even; a row denominator with a factor 3 costs one
+// float64 multiply by 1/3 (a second rounding).  Windows with a non-finite
+// value or a largest magnitude outside 2^-923 .. 2^977 return false (the
+// caller uses float64 there).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fixed_split62(double v, int E, int& nh, int& nl) {
+  const long long bits = __double_as_longlong(v);
+  const int e = (int)((bits >> 52) & 0x7ff);
+  const unsigned long long M = (unsigned long long)(bits & 0xFFFFFFFFFFFFFll) | (e ? (1ull << 52) : 0ull);
+  const int sh = max(e, 1) - E + 9;  // <= 9: |n| = M 2^sh < 2^62
+  unsigned long long N;
+  if (sh >= 0) N = M << sh;
+  else N = -sh <= 54 ? ((M >> (-sh - 1)) + 1) >> 1 : 0ull;  // half away from zero
+  const int h = (int)(N >> 31), l = (int)(N & 0x7fffffffull);
+  nh = bits < 0 ? -h : h;
+  nl = bits < 0 ? -l : l;
+}
+
+__device__ __forceinline__ double fixed128_to_f64(long long A, long long B, int sh, bool third) {
+  const __int128 T = ((__int128)A << 31) + (__int128)B;
+  if (T == 0) return 0.0;
+  const bool neg = T < 0;
+  unsigned __int128 N = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
+  const unsigned long long hi0 = (unsigned long long)(N >> 64), lo0 = (unsigned long long)N;
+  const int lz = hi0 ? __clzll((long long)hi0) : 64 + __clzll((long long)lo0);
+  N <<= lz;  // leading one at bit 127
+  const unsigned long long X = (unsigned long long)(N >> 64);
+  const bool sticky = ((unsigned long long)N != 0ull) || (X & 0x3FFull);
+  unsigned long long mant = X >> 11;  // 53 bits
+  int e2 = 127 - lz;                  // N in [2^e2, 2^(e2+1))
+  if (((X >> 10) & 1ull) && (sticky || (mant & 1ull))) ++mant;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++e2;
+  }
+  const long long be = 1023 + e2 - sh;  // in the normal range for the windows served
+  const double d = __longlong_as_double((long long)((unsigned long long)neg << 63 | (unsigned long long)be << 52 |
+                                                    (mant & 0xFFFFFFFFFFFFFull)));
+  return third ? d * (1.0 / 3.0) : d;
+}
+
+template <typename Store>
+__device__ __forceinline__ bool restrict_fixed_layers(const double* v, int L, int m, int k, const Store& store) {
+  int E = 1;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    if (i < L) E = max(E, (int)((__double_as_longlong(v[i]) >> 52) & 0x7ff));
+  if (E < 100 || E > 2000) return false;
+  int nh[5], nl[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    nh[i] = 0;
+    nl[i] = 0;
+    if (i < L) fixed_split62(v[i], E, nh[i], nl[i]);
+  }
+  const int s = 1084 - E;
+  for (int j = 1; j < k; ++j) {
+    const int r0 = rw_index(m, k, j);
+    long long A = 0, B = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const int W = c_rwx[r0 + i];
+      A += (long long)W * nh[i];
+      B += (long long)W * nl[i];
+    }
+    const int den = c_rw_den[r0 / 5];
+    store(j, fixed128_to_f64(A, B, s + (den & 15), (den >> 4) != 0));
+  }
+  return true;
+}
+
+// Restriction precision modes: float64 throughout (float64 plans); split
+// (float64 first extrapolated layer, float-pair second layer, float32
+// d-linear averaging on exact float-pair differences); fixed (the exact
+// integer Taylor layers above for finite-difference items, float64 for the
+// windows they do not serve, least-squares items and d-linear).
+constexpr int kRestrictF64 = 0, kRestrictSplit = 1, kRestrictFixed = 2;
 
 template <int RP>
 __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* __restrict__ items,
@@ -798,9 +887,11 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
     int s, L;
     stencil_window(k - 1, -k, k - 1, pure_exactness(m), s, L);
     const int pos = k - 1 - s;
+    // fine layer 1 lies outside the window only for Taylor-2 with k = 5
+    const bool inj_in = 1 - s >= 0 && 1 - s < L;
     constexpr int R = 2;
     for (int e0 = threadIdx.x; e0 < ntask; e0 += R * blockDim.x) {
-      double v[R][5];
+      double v[R][5], v1[R];
       double* ccol[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -810,6 +901,7 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
         const bool ok = e0 + r * (int)blockDim.x < ntask;
 #pragma unroll
         for (int i = 0; i < 5; ++i) v[r][i] = (ok && i < L) ? __ldg(fcol + (s + i) * gs_n) : 0.0;
+        v1[r] = (ok && !inj_in) ? __ldg(fcol + gs_n) : 0.0;
         if (!ok) ccol[r] = nullptr;
         c.advance(nu, t.na, t.nb);
       }
@@ -817,7 +909,10 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
       for (int r = 0; r < R; ++r) {
         if (!ccol[r]) continue;
         double* col = ccol[r];
-        col[0] = pick5(v[r], 1 - s);  // layer 0 coincides with fine layer 1
+        col[0] = inj_in ? pick5(v[r], 1 - s) : v1[r];  // layer 0 coincides with fine layer 1
+        if (RP == kRestrictFixed && it.scheme == 0 &&
+            restrict_fixed_layers(v[r], L, m, k, [&](int j, double out) { col[j * gs_n] = out; }))
+          continue;
         if (SPLIT) {
           // layer 1 with float64 combined weights (the float64 unit is idle
           // here); layer 2 in float64 for the first column of the pair and in
@@ -835,8 +930,15 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
               for (int i = 0; i < 5; ++i) acc2 = fma(w2[i], v[r][i], acc2);
               col[2 * gs_n] = acc2;
             } else {
-              taylor_extrapolate_split(v[r], L, pos, m, k, 2, it.scheme, [&](int j, double out) { col[j * gs_n] = out; });
+              taylor_extrapolate_split(v[r], L, pos, m, k, 2, 3, it.scheme, [&](int j, double out) { col[j * gs_n] = out; });
             }
+          }
+          for (int j = 3; j < k; ++j) {  // overlaps 4 and 5: deeper layers in float64
+            const double* w = c_rw + rw_index(m, k, j, it.scheme);
+            double acc = 0.0;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) acc = fma(w[i], v[r][i], acc);
+            col[j * gs_n] = acc;
           }
         } else {
           for (int j = 1; j < k; ++j) {

@@ -66,7 +66,8 @@ def _item(**kw):
 @pytest.mark.parametrize("bad,status", [
     (dict(face=6), 1), (dict(face=-1), 1), (dict(subface=9), 1), (dict(subface=-2), 1),
     (dict(order=0), 1), (dict(order=4), 1), (dict(patch_size=0), 1), (dict(overlap=0), 1),
-    (dict(patch_size=3), 2), (dict(overlap=4, patch_size=12), 2), (dict(patch_size=51), 2),
+    (dict(patch_size=3), 2), (dict(overlap=6, patch_size=12), 2), (dict(overlap=4, patch_size=10), 2),
+    (dict(overlap=5, patch_size=12, scheme=1), 2), (dict(patch_size=51), 2),
     (dict(order=2, overlap=1), 2), (dict(order=3, overlap=1), 2), (dict(scheme=2), 1), (dict(scheme=-1), 1),
     (dict(scheme=1, order=1), 2),
     (dict(coarse_offset=-1), 1), (dict(fine_offset=1), 1), (dict(coarse_offset=1), 1),
@@ -116,3 +117,12 @@ def test_overlapping_outputs_rejected(lib):
     items = [_item(subface=0, coarse_offset=0, fine_offset=0), _item(subface=1, coarse_offset=arr // 2, fine_offset=arr)]
     st, _ = _create(items, U=U, cl=2 * arr, fl=2 * arr)
     assert st == 1
+
+
+def test_deep_overlap_needs_factorised_kernels(lib):
+    """Overlaps 4 and 5 are served by the factorised kernels only: a plan that
+    routes them to the sparse-row kernels is refused on the host."""
+    st, h = _create([_item(overlap=4, patch_size=12)], flags=B.FLAG_CSR)
+    assert st == 2 and h.value is None
+    st, h = _create([_item(overlap=5, patch_size=9, order=1)], flags=B.FLAG_CSR)
+    assert st == 2 and h.value is None

@@ -254,3 +254,32 @@ def test_full_size_puncture_batch(precision, tol):
     record(test="full_size_puncture", precision=precision, worst=worst)
     assert worst <= tol, worst
     plan.close()
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_fixed_restriction_windows(order):
+    """Fixed-point Taylor restriction: exact integer layers for windows whose
+    largest magnitude lies in 2^-923 .. 2^977, float64 outside.  Unknowns
+    sit on both sides of both ends of that range, spread over twenty decades
+    inside one window, or hold a NaN; every one matches the oracle at the
+    float64 tolerance (NaN where the oracle gives NaN)."""
+    U = 8
+    items, c, f = _faces(U, order, 30 + order, p=9)
+    rng = np.random.default_rng(77 + order)
+    scales = np.array([1.0, 2.0 ** -922, 2.0 ** -925, 2.0 ** 975, 2.0 ** 978, 1.0, 3.5e5, 1.0])
+    f = (f.reshape(-1, U) * scales).copy()
+    f[:, 5] *= 10.0 ** rng.uniform(-20.0, 0.0, len(f))
+    fo = int(items[3]["fine_offset"])
+    f[fo // U:fo // U + 2 * 3 * 81, 7] = np.nan  # face 3, unknown 7: the first fine face array
+    f = f.reshape(-1)
+    plan = B.Plan(items, U, len(c), len(f), B.PREC_FIXED)
+    _, cm = written_masks(items, U, len(c), len(f))
+    c_ref = tr.restrict(items, U, f, c)
+    c_gpu = gpu_restrict(plan, f, c)
+    plan.close()
+    assert np.array_equal(np.isnan(c_gpu[cm]), np.isnan(c_ref[cm]))
+    assert np.isnan(c_ref[cm]).any()
+    ok = cm & ~np.isnan(c_ref)
+    e_r, rms = normwise_errors(items, U, c_gpu, c_ref, ok, "coarse")
+    record(test="fixed_restriction_windows", order=order, restrict=e_r, rms=rms)
+    assert e_r <= FP64_TOL, e_r

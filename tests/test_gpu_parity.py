@@ -87,6 +87,19 @@ def test_subface_items(order, p, k, precision, tol):
     _check(items, 7, c, f, precision, tol)
 
 
+@pytest.mark.parametrize("precision,tol", PRECISIONS)
+@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("k", [4, 5])
+def test_overlaps_four_and_five(k, order, precision, tol):
+    """Overlaps 4 and 5: fine ghost layers -4..-k come from the second layer
+    of coarse centres, the deeper coarse halo layers are extrapolated from
+    fine layer k - 1 (coarse layer 1 of k = 5 is an injection).  All six
+    faces, whole faces and subfaces, p = 9 and 12, ragged unknown count."""
+    faces, subs, ps = [0, 1, 2, 3, 4, 5], [-1, 4, -1, 0, 8, -1], [9, 12, 9, 9, 12, 9]
+    items, c, f = _batch(faces, subs, ps, [k] * 6, [order] * 6, 11, seed=40 + 3 * k + order)
+    _check(items, 11, c, f, precision, tol)
+
+
 def test_dlinear_overlap_one():
     n = 6
     items, c, f = _batch(list(range(6)), [-1] * n, [6] * n, [1] * n, [1] * n, 3, seed=5)

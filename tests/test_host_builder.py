@@ -82,7 +82,8 @@ def test_least_squares_class_tables_match_oracle(harness, p, k, order, sub):
 
 
 @pytest.mark.parametrize("p,k,order,sub", [(9, 3, 3, -1), (12, 3, 3, -1), (6, 2, 2, -1), (16, 3, 3, 4), (24, 3, 1, -1),
-                                           (48, 3, 3, -1), (7, 3, 3, -1), (4, 2, 3, 0), (9, 1, 1, -1)])
+                                           (48, 3, 3, -1), (7, 3, 3, -1), (4, 2, 3, 0), (9, 1, 1, -1),
+                                           (9, 4, 3, -1), (9, 5, 3, 4), (12, 5, 2, -1), (9, 4, 1, -1), (9, 5, 1, 7)])
 @pytest.mark.parametrize("budget", [64 * 1024, 112 * 1024])
 def test_fixed_point_tiles_fit_their_launch(harness, p, k, order, sub, budget):
     """Fixed-point plans (precision 2): every tile of the fixed-point kernel
