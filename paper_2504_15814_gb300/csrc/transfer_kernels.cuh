@@ -36,8 +36,6 @@ __constant__ float c_ls_f[LS_SIZE];
 __constant__ double c_rw[RW_SIZE];
 __constant__ float c_rw_hi[RW_SIZE];
 __constant__ float c_rw_lo[RW_SIZE];
-__constant__ int32_t c_rwx[RW_SIZE];       // integer restriction weights (Tables::rwx)
-__constant__ int32_t c_rw_den[RW_SIZE / 5];  // their row denominators 2^a 3^b as a | b << 4
 
 template <bool SPLIT> struct Arith;
 template <> struct Arith<false> {
@@ -758,91 +756,10 @@ __device__ __forceinline__ void dlinear_restrict_split(const Fine& F, const Coar
   }
 }
 
-// ---------------------------------------------------------------------------
-// Exact Taylor restriction of one column (fixed-point plans).  The window
-// values v[0..L) are rounded once onto the grid 2^-s with s = 1084 - E (E the
-// largest biased exponent of the window), |n| < 2^62, so the rounding error
-// is at most 2^-62 of the window's largest magnitude; each n is carried as
-// two signed 31-bit halves, so the weighted sums over the integer weights
-// (|W| < 2^15) are exact in two int64 accumulators, A (high halves) and B.
-// The result T 2^-s / D, T = A 2^31 + B, is normalised from 128 bits with
-// one round-to-nearest-even; a row denominator with a factor 3 costs one
-// float64 multiply by 1/3 (a second rounding).  Windows with a non-finite
-// value or a largest magnitude outside 2^-923 .. 2^977 return false (the
-// caller uses float64 there).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void fixed_split62(double v, int E, int& nh, int& nl) {
-  const long long bits = __double_as_longlong(v);
-  const int e = (int)((bits >> 52) & 0x7ff);
-  const unsigned long long M = (unsigned long long)(bits & 0xFFFFFFFFFFFFFll) | (e ? (1ull << 52) : 0ull);
-  const int sh = max(e, 1) - E + 9;  // <= 9: |n| = M 2^sh < 2^62
-  unsigned long long N;
-  if (sh >= 0) N = M << sh;
-  else N = -sh <= 54 ? ((M >> (-sh - 1)) + 1) >> 1 : 0ull;  // half away from zero
-  const int h = (int)(N >> 31), l = (int)(N & 0x7fffffffull);
-  nh = bits < 0 ? -h : h;
-  nl = bits < 0 ? -l : l;
-}
-
-__device__ __forceinline__ double fixed128_to_f64(long long A, long long B, int sh, bool third) {
-  const __int128 T = ((__int128)A << 31) + (__int128)B;
-  if (T == 0) return 0.0;
-  const bool neg = T < 0;
-  unsigned __int128 N = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
-  const unsigned long long hi0 = (unsigned long long)(N >> 64), lo0 = (unsigned long long)N;
-  const int lz = hi0 ? __clzll((long long)hi0) : 64 + __clzll((long long)lo0);
-  N <<= lz;  // leading one at bit 127
-  const unsigned long long X = (unsigned long long)(N >> 64);
-  const bool sticky = ((unsigned long long)N != 0ull) || (X & 0x3FFull);
-  unsigned long long mant = X >> 11;  // 53 bits
-  int e2 = 127 - lz;                  // N in [2^e2, 2^(e2+1))
-  if (((X >> 10) & 1ull) && (sticky || (mant & 1ull))) ++mant;
-  if (mant >> 53) {
-    mant >>= 1;
-    ++e2;
-  }
-  const long long be = 1023 + e2 - sh;  // in the normal range for the windows served
-  const double d = __longlong_as_double((long long)((unsigned long long)neg << 63 | (unsigned long long)be << 52 |
-                                                    (mant & 0xFFFFFFFFFFFFFull)));
-  return third ? d * (1.0 / 3.0) : d;
-}
-
-template <typename Store>
-__device__ __forceinline__ bool restrict_fixed_layers(const double* v, int L, int m, int k, const Store& store) {
-  int E = 1;
-#pragma unroll
-  for (int i = 0; i < 5; ++i)
-    if (i < L) E = max(E, (int)((__double_as_longlong(v[i]) >> 52) & 0x7ff));
-  if (E < 100 || E > 2000) return false;
-  int nh[5], nl[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    nh[i] = 0;
-    nl[i] = 0;
-    if (i < L) fixed_split62(v[i], E, nh[i], nl[i]);
-  }
-  const int s = 1084 - E;
-  for (int j = 1; j < k; ++j) {
-    const int r0 = rw_index(m, k, j);
-    long long A = 0, B = 0;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      const int W = c_rwx[r0 + i];
-      A += (long long)W * nh[i];
-      B += (long long)W * nl[i];
-    }
-    const int den = c_rw_den[r0 / 5];
-    store(j, fixed128_to_f64(A, B, s + (den & 15), (den >> 4) != 0));
-  }
-  return true;
-}
-
-// Restriction precision modes: float64 throughout (float64 plans); split
-// (float64 first extrapolated layer, float-pair second layer, float32
-// d-linear averaging on exact float-pair differences); fixed (the exact
-// integer Taylor layers above for finite-difference items, float64 for the
-// windows they do not serve, least-squares items and d-linear).
-constexpr int kRestrictF64 = 0, kRestrictSplit = 1, kRestrictFixed = 2;
+// Restriction precision modes: float64 throughout (float64 and fixed-point
+// plans), or split (float64 first extrapolated layer, float-pair second
+// layer, float32 d-linear averaging on exact float-pair differences).
+constexpr int kRestrictF64 = 0, kRestrictSplit = 1;
 
 template <int RP>
 __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* __restrict__ items,
@@ -910,9 +827,6 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
         if (!ccol[r]) continue;
         double* col = ccol[r];
         col[0] = inj_in ? pick5(v[r], 1 - s) : v1[r];  // layer 0 coincides with fine layer 1
-        if (RP == kRestrictFixed && it.scheme == 0 &&
-            restrict_fixed_layers(v[r], L, m, k, [&](int j, double out) { col[j * gs_n] = out; }))
-          continue;
         if (SPLIT) {
           // layer 1 with float64 combined weights (the float64 unit is idle
           // here); layer 2 in float64 for the first column of the pair and in

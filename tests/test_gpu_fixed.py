@@ -258,11 +258,11 @@ def test_full_size_puncture_batch(precision, tol):
 
 @pytest.mark.parametrize("order", [2, 3])
 def test_fixed_restriction_windows(order):
-    """Fixed-point Taylor restriction: exact integer layers for windows whose
-    largest magnitude lies in 2^-923 .. 2^977, float64 outside.  Unknowns
-    sit on both sides of both ends of that range, spread over twenty decades
-    inside one window, or hold a NaN; every one matches the oracle at the
-    float64 tolerance (NaN where the oracle gives NaN)."""
+    """Restriction of fixed-point plans (float64 arithmetic) on adversarial
+    windows: unknowns scaled to 2^-925 .. 2^978, values spread over twenty
+    decades inside one window, a NaN in one fine face array; every unknown
+    matches the oracle at the float64 tolerance (NaN where the oracle gives
+    NaN)."""
     U = 8
     items, c, f = _faces(U, order, 30 + order, p=9)
     rng = np.random.default_rng(77 + order)

@@ -107,14 +107,18 @@ def test_dlinear_overlap_one():
 
 
 def test_mixed_batch_and_large_patches():
-    # uneven batch: p in {6, 9, 12, 24, 48}, k in {2, 3}, orders mixed, U = 5
+    # uneven batch: p in {6, 9, 12}, k in {2, 3}, orders mixed, whole faces
+    # and subfaces, U = 5; plus one subface of p = 24 (Taylor-3) and one of
+    # p = 48 (Taylor-2, k = 2)
     rng = np.random.default_rng(3)
-    n = 40
-    ps = rng.choice([6, 9, 12, 24, 48], n)
+    n = 26
+    ps = rng.choice([6, 9, 12], n)
     ks = rng.choice([2, 3], n)
     orders = rng.choice([1, 2, 3], n)
     faces = rng.integers(0, 6, n)
     subs = rng.integers(-1, 9, n)
+    subs[2:6] = -1
+    ps[:2], ks[:2], orders[:2], subs[:2], faces[:2] = [24, 48], [3, 2], [3, 2], [4, 0], [1, 5]
     items, c, f = _batch(faces, subs, ps, ks, orders, 5, seed=7)
     _check(items, 5, c, f, B.PREC_FP64, FP64_TOL)
     _check(items, 5, c, f, B.PREC_FIXED, FP64_TOL)
