@@ -35,16 +35,16 @@ constexpr int kAdjBits = 44;  // quantized gradients satisfy |n| < 2^44
 constexpr int kAdjThreads = 256;
 
 // round(x 2^s) for a float64 x with |x| < 2^(44 - s): exact shift of the
-// significand (no float64 instruction), ties away from zero.
+// significand (no float64 instruction), ties away from zero.  The bound puts
+// x 2^s = m 2^-r with r = 1075 - s - E >= 9, so the shift is always to the
+// right: floor(m / 2^(r-1)), plus one, halved.  Subnormal x give 0.
 __device__ __forceinline__ long long quantize_pow2(double x, int s) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((b >> 52) & 0x7ffull);
-  unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;
-  const int sh = E - 1075 + s;  // x 2^s = m 2^sh
-  long long n;
-  if (E == 0 || sh < -63) n = 0;
-  else if (sh >= 0) n = (long long)(m << sh);  // sh <= 0 for |x| < 2^(44 - s) < 2^(53 - s)
-  else n = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;
+  const int r1 = min(1074 - s - E, 63);  // r - 1 >= 8; m < 2^53 gives 0 from 53 on
+  const unsigned long long t = E ? (m >> r1) : 0ull;
+  const long long n = (long long)((t + 1ull) >> 1);
   return (long long)(b >> 63) ? -n : n;
 }
 
