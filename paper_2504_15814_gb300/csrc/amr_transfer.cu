@@ -138,6 +138,9 @@ struct amr_transfer_plan {
   int n_pt_tiles = 0, n_rt_tiles = 0;
   amr::AdjointTile *pt_tiles_d = nullptr, *rt_tiles_d = nullptr;
   int n_fx_pt_tiles = 0, n_rtt_tiles = 0, fx_adj_smem = 0;
+  // whether the factorised kernels write every value of the gradient buffer
+  // (then the adjoint calls need no zero fill first)
+  bool pt_covers = false, rt_covers = false;
   amr::AdjointTile* fx_pt_tiles_d = nullptr;
   amr::Tile* rtt_tiles_d = nullptr;
   int32_t *group_ptr_d = nullptr, *group_items_d = nullptr, *item_class_d = nullptr;
@@ -226,6 +229,32 @@ static amr_status ensure_adjoint(amr_transfer_plan* p) {
   }
   p->n_fx_pt_tiles = (int)ab.fx_pt_tiles.size();
   p->n_rtt_tiles = (int)ab.rt_taylor_tiles.size();
+  // coverage: the arrays the factorised kernels overwrite, sorted, must tile
+  // [0, elems) without gaps, and no item may be left to the sparse-row kernels
+  auto covers = [](std::vector<std::pair<int64_t, int64_t>>& iv, int64_t elems) {
+    std::sort(iv.begin(), iv.end());
+    int64_t at = 0;
+    for (const auto& r : iv) {
+      if (r.first > at) return false;
+      at = std::max(at, r.second);
+    }
+    return at >= elems;
+  };
+  {
+    std::vector<std::pair<int64_t, int64_t>> iv;
+    for (const amr::AdjointTile& t : ab.fx_pt_tiles) {
+      const amr_transfer_item& x = p->items_h[ab.group_items[ab.group_ptr[t.index]]];
+      iv.push_back({x.coarse_offset, x.coarse_offset + 2LL * x.overlap * x.patch_size * x.patch_size * p->U});
+    }
+    p->pt_covers = ab.pt_tiles.empty() && covers(iv, p->coarse_elems);
+    iv.clear();
+    for (const amr::Tile& t : ab.rt_taylor_tiles) {
+      const amr_transfer_item& x = p->items_h[t.item];
+      const int64_t arr = 2LL * x.overlap * x.patch_size * x.patch_size * p->U;
+      iv.push_back({x.fine_offset + t.slot * arr, x.fine_offset + (t.slot + 1) * arr});
+    }
+    p->rt_covers = ab.rt_tiles.empty() && covers(iv, p->fine_elems);
+  }
   p->fx_adj_smem = ab.fx_smem;
   p->n_pt_tiles = (int)ab.pt_tiles.size();
   p->n_rt_tiles = (int)ab.rt_tiles.size();
@@ -570,7 +599,7 @@ amr_status amr_transfer_plan_interpolate_adjoint(amr_transfer_plan* p, const dou
   if (st != AMR_OK) return st;
   if ((st = ensure_adjoint(p)) != AMR_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  if (p->coarse_elems > 0) AMR_CUDA(cudaMemsetAsync(g_coarse, 0, (size_t)p->coarse_elems * 8, s));
+  if (p->coarse_elems > 0 && !p->pt_covers) AMR_CUDA(cudaMemsetAsync(g_coarse, 0, (size_t)p->coarse_elems * 8, s));
   if (p->n_fx_pt_tiles > 0) {
     amr::interp_adjoint_fixed_kernel<<<p->n_fx_pt_tiles, amr::kAdjThreads, p->fx_adj_smem, s>>>(
         p->items_d, p->fx_pt_tiles_d, p->group_ptr_d, p->group_items_d, p->U, g_fine, g_coarse);
@@ -591,7 +620,7 @@ amr_status amr_transfer_plan_restrict_adjoint(amr_transfer_plan* p, const double
   if (st != AMR_OK) return st;
   if ((st = ensure_adjoint(p)) != AMR_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  if (p->fine_elems > 0) AMR_CUDA(cudaMemsetAsync(g_fine, 0, (size_t)p->fine_elems * 8, s));
+  if (p->fine_elems > 0 && !p->rt_covers) AMR_CUDA(cudaMemsetAsync(g_fine, 0, (size_t)p->fine_elems * 8, s));
   if (p->n_rtt_tiles > 0) {
     amr::restrict_adjoint_taylor_kernel<<<p->n_rtt_tiles, kThreads, 0, s>>>(p->items_d, p->rtt_tiles_d, p->U,
                                                                             g_coarse, g_fine);

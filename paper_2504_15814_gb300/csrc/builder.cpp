@@ -764,29 +764,16 @@ AdjointBuild build_adjoint(const amr_transfer_desc& desc) {
     const amr_transfer_item& x = desc.items[it];
     const int nsub = x.subface < 0 ? 9 : 1;
     // direct R^T of Taylor items, p a multiple of 3 (each coarse halo column
-    // reaches only its own coincident fine column)
+    // reaches only its own coincident fine column): one tile per fine face
+    // array, which the kernel writes whole
     if (x.order >= 2 && x.patch_size % 3 == 0 && !(desc.flags & AMR_FLAG_CSR)) {
-      const int p = x.patch_size;
       for (int sl = 0; sl < nsub; ++sl) {
-        const int sub = x.subface < 0 ? sl : x.subface;
-        int oa0, oa1, ob0, ob1;
-        owned_range(sub % 3, p, oa0, oa1);
-        owned_range(sub / 3, p, ob0, ob1);
-        for (int a0 = oa0; a0 < oa1; a0 += 12)
-          for (int b0 = ob0; b0 < ob1; b0 += 12)
-            for (int64_t u0 = 0; u0 < U; u0 += 128) {
-              Tile t{};
-              t.item = (int32_t)it;
-              t.sub = (int8_t)sub;
-              t.slot = (int8_t)(x.subface < 0 ? sl : 0);
-              t.na = (int8_t)std::min(12, oa1 - a0);
-              t.nb = (int8_t)std::min(12, ob1 - b0);
-              t.a0 = (int16_t)a0;
-              t.b0 = (int16_t)b0;
-              t.u0 = (int16_t)u0;
-              t.nu = (int16_t)std::min<int64_t>(128, U - u0);
-              ab.rt_taylor_tiles.push_back(t);
-            }
+        Tile t{};
+        t.item = (int32_t)it;
+        t.sub = (int8_t)(x.subface < 0 ? sl : x.subface);
+        t.slot = (int8_t)(x.subface < 0 ? sl : 0);
+        t.nu = (int16_t)U;
+        ab.rt_taylor_tiles.push_back(t);
       }
       continue;
     }

@@ -133,7 +133,7 @@ struct AdjointBuild {
   // factorised work: P^T of the groups whose items all use finite
   // differences with p a multiple of 3 (fixed-point kernel, 32-unknown
   // chunks, fx_smem bytes of shared memory), R^T of the Taylor items with p a
-  // multiple of 3 (restriction tiles over their owned coarse columns)
+  // multiple of 3 (one tile per fine face array: item, sub, slot)
   std::vector<AdjointTile> fx_pt_tiles;
   int fx_smem = 0;
   std::vector<Tile> rt_taylor_tiles;

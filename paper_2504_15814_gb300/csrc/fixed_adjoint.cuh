@@ -25,7 +25,9 @@
 // from its coincident fine column only (injection at coarse layer 0,
 // combined extrapolation weights W_j for the deeper layers), so R^T of one
 // column is a 5 x 3 product: fine layer s + i of the window receives
-// [s + i == 1] g_0 + sum_{j >= 1} W_j[i] g_j.
+// [s + i == 1] g_0 + sum_{j >= 1} W_j[i] g_j.  R^T overwrites the whole fine
+// buffer, so the kernel writes every value of its fine face arrays: zeros
+// by flat 16-byte stores, then the window values.
 #pragma once
 #include "fixed_kernels.cuh"
 
@@ -33,6 +35,19 @@ namespace amr {
 
 constexpr int kAdjBits = 44;  // quantized gradients satisfy |n| < 2^44
 constexpr int kAdjThreads = 256;
+
+// L2 eviction policy for loads that are the last use of their lines (PTX
+// createpolicy), so that they do not displace lines other CTAs read again.
+__device__ __forceinline__ unsigned long long l2_policy_evict_first() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ double ld_hint(const double* ptr, unsigned long long pol) {
+  double v;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
 
 // round(x 2^s) for a float64 x with |x| < 2^(44 - s): exact shift of the
 // significand (no float64 instruction), ties away from zero.  The bound puts
@@ -303,6 +318,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
         const double* fc = g_fine + it.fine_offset + slot * arr +
                            frame_vol(fr, -1, 3 * a + 1 - s0 * p, 3 * b + 1 - s1 * p) * U + t.u0 + lane;
         // all 27 loads first (independent, in flight together), then the rounding
+        const unsigned long long last = l2_policy_evict_first();
         double gv[3][3][3];
 #pragma unroll
         for (int ii = 0; ii < 3; ++ii)
@@ -310,7 +326,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
           for (int e0 = 0; e0 < 3; ++e0)
 #pragma unroll
             for (int e1 = 0; e1 < 3; ++e1)
-              gv[ii][e0][e1] = __ldg(fc - min(ii, k - 1) * gs_n + (e0 - 1) * gs_a + (e1 - 1) * gs_b);
+              gv[ii][e0][e1] = ld_hint(fc - min(ii, k - 1) * gs_n + (e0 - 1) * gs_a + (e1 - 1) * gs_b, last);
         long long n[3][3][3];  // [ii][e0 + 1][e1 + 1]
 #pragma unroll
         for (int ii = 0; ii < 3; ++ii)
@@ -374,9 +390,13 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
 }
 
 // g_fine = R^T g_coarse for the Taylor items (finite differences or least
-// squares) with p a multiple of 3: one thread per (coarse halo column,
-// unknown), float64.  Writes only the fine window entries; the caller zeroes
-// the fine buffer first.
+// squares) with p a multiple of 3: one CTA per fine face array, which it
+// writes whole.  First the array is zeroed with flat 16-byte stores (memory
+// order, full sectors); then, after a barrier, the derivative window of each
+// coincident column (fine local indices q0, q1 = 1 mod 3) is written: fine
+// layer s + i gets [s + i == 1] g_0 + sum_{j >= 1} W_j[i] g_j from coarse halo
+// column ((q0 + s0 p - 1) / 3, (q1 + s1 p - 1) / 3); one warp per window
+// volume, lane = unknown.
 __global__ void __launch_bounds__(256) restrict_adjoint_taylor_kernel(const amr_transfer_item* __restrict__ items,
                                                                       const Tile* __restrict__ tiles, int U,
                                                                       const double* __restrict__ g_coarse,
@@ -386,29 +406,31 @@ __global__ void __launch_bounds__(256) restrict_adjoint_taylor_kernel(const amr_
   const int p = it.patch_size, k = it.overlap, m = it.order;
   const FaceFrame fr = face_frame(it.face, p, k);
   const int64_t arr = fr.vols * U;
+  double* fa = g_fine + it.fine_offset + (int64_t)t.slot * arr;
+  {
+    const int head = (reinterpret_cast<uintptr_t>(fa) & 15) ? 1 : 0;  // fa is 8-byte aligned
+    const int64_t n2 = (arr - head) / 2;
+    double2* v2 = reinterpret_cast<double2*>(fa + head);
+    for (int64_t q = threadIdx.x; q < n2; q += blockDim.x) v2[q] = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0 && head) fa[0] = 0.0;
+    if (threadIdx.x == 0 && head + 2 * n2 < arr) fa[arr - 1] = 0.0;
+  }
+  __syncthreads();
+  const int s0 = t.sub % 3, s1 = t.sub / 3;
   const int gs_n = (int)fr.s_n * U;
   int s, L;
   stencil_window(k - 1, -k, k - 1, pure_exactness(m), s, L);
-  const int ntask = t.na * t.nb * t.nu;
-  for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
-    const int u = e % t.nu, c2 = e / t.nu;
-    const int a = t.a0 + c2 % t.na, b = t.b0 + c2 / t.na;
-    const int s0 = t.sub >= 0 ? t.sub % 3 : (3 * a) / p, s1 = t.sub >= 0 ? t.sub / 3 : (3 * b) / p;
-    const int slot = t.sub >= 0 ? t.slot : s0 + 3 * s1;
-    const double* gc = g_coarse + it.coarse_offset + frame_vol(fr, 0, a, b) * U + t.u0 + u;
-    double g[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      if (j < k) g[j] = __ldg(gc + j * gs_n);
-    double* fcol = g_fine + it.fine_offset + (int64_t)slot * arr +
-                   frame_vol(fr, 0, 3 * a + 1 - s0 * p, 3 * b + 1 - s1 * p) * U + t.u0 + u;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      if (i < L) {
-        double v = (s + i == 1) ? g[0] : 0.0;  // coarse layer 0 injects fine layer 1
-        for (int j = 1; j < k; ++j) v = fma(c_rw[rw_index(m, k, j, it.scheme) + i], g[j], v);
-        fcol[(s + i) * gs_n] = v;
-      }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nc = p / 3;  // coincident columns per axis
+  for (int w = warp; w < nc * nc * L; w += nw) {
+    const int i = w % L, cc = w / L;
+    const int q0 = 3 * (cc % nc) + 1, q1 = 3 * (cc / nc) + 1;
+    const double* gc = g_coarse + it.coarse_offset + frame_vol(fr, 0, (q0 + s0 * p - 1) / 3, (q1 + s1 * p - 1) / 3) * U;
+    double* dst = fa + frame_vol(fr, s + i, q0, q1) * U;
+    for (int u = lane; u < U; u += 32) {
+      double val = s + i == 1 ? __ldg(gc + u) : 0.0;  // coarse layer 0 injects fine layer 1
+      for (int jj = 1; jj < k; ++jj) val = fma(c_rw[rw_index(m, k, jj, it.scheme) + i], __ldg(gc + jj * gs_n + u), val);
+      dst[u] = val;
     }
   }
 }
