@@ -601,6 +601,9 @@ amr_status amr_transfer_plan_interpolate_adjoint(amr_transfer_plan* p, const dou
   cudaStream_t s = (cudaStream_t)stream;
   if (p->coarse_elems > 0 && !p->pt_covers) AMR_CUDA(cudaMemsetAsync(g_coarse, 0, (size_t)p->coarse_elems * 8, s));
   if (p->n_fx_pt_tiles > 0) {
+    amr::adjoint_emax_kernel<<<p->n_fx_pt_tiles, amr::kAdjThreads, 0, s>>>(
+        p->items_d, p->fx_pt_tiles_d, p->group_ptr_d, p->group_items_d, p->U, g_fine, g_coarse);
+    AMR_CUDA(cudaGetLastError());
     amr::interp_adjoint_fixed_kernel<<<p->n_fx_pt_tiles, amr::kAdjThreads, p->fx_adj_smem, s>>>(
         p->items_d, p->fx_pt_tiles_d, p->group_ptr_d, p->group_items_d, p->U, g_fine, g_coarse);
     AMR_CUDA(cudaGetLastError());

@@ -218,19 +218,19 @@ __device__ __forceinline__ void dlinear_fixed_adjoint(const Grad& grad, const Ad
 }
 
 // ---------------------------------------------------------------------------
-// g_coarse = P^T g_fine, fixed point, for one group of items sharing a
-// coarse face array (finite-difference items, p a multiple of 3) and a chunk
-// of <= 32 unknowns.  One warp per coarse centre, lane = unknown.  Writes
-// every value of the group's coarse face array (zero where nothing reaches).
-// rn_lo / rn_hi: signed normal layers of the accumulator (the union of the
-// items' stencil regions).
+// First step of the fixed-point P^T: per group of items sharing a coarse face
+// array and chunk of <= 32 unknowns, the largest biased exponent of the
+// group's ghost gradients per unknown (the grid of the exact accumulation).
+// It is left, as an integer, in the first volume of the group's coarse face
+// array (g_coarse, which interp_adjoint_fixed_kernel reads and then
+// overwrites).  A separate light kernel streams the gradients at high
+// occupancy; inside the accumulation kernel (two CTAs per SM) the same scan
+// ran at about half the bandwidth.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kAdjThreads, 2)
-    interp_adjoint_fixed_kernel(const amr_transfer_item* __restrict__ items, const AdjointTile* __restrict__ tiles,
-                                const int32_t* __restrict__ group_ptr, const int32_t* __restrict__ group_items, int U,
-                                const double* __restrict__ g_fine, double* __restrict__ g_coarse) {
-  extern __shared__ double smem_raw[];
-  long long* acc = reinterpret_cast<long long*>(smem_raw);
+__global__ void __launch_bounds__(kAdjThreads)
+    adjoint_emax_kernel(const amr_transfer_item* __restrict__ items, const AdjointTile* __restrict__ tiles,
+                        const int32_t* __restrict__ group_ptr, const int32_t* __restrict__ group_items, int U,
+                        const double* __restrict__ g_fine, double* __restrict__ g_coarse) {
   __shared__ int s_emax[32];
   const AdjointTile t = tiles[blockIdx.x];
   const int m0 = group_ptr[t.index], m1 = group_ptr[t.index + 1];
@@ -238,25 +238,13 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
   const int p = first.patch_size, k = first.overlap;
   const FaceFrame fr = face_frame(first.face, p, k);
   const int64_t arr = fr.vols * U;
-  int rlo = 0, rhi = -1;  // union of the items' normal stencil ranges
-  for (int mi = m0; mi < m1; ++mi) {
-    IRange rn, ra, rb;
-    interp_region(p, k, items[group_items[mi]].order, 0, p, 0, p, rn, ra, rb);
-    rlo = min(rlo, rn.lo);
-    rhi = max(rhi, rn.hi);
-  }
-  const int NJ = rhi - rlo + 1, npts = NJ * p * p;
   const int nu = t.nu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t dyn_smem;
-  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
-  if ((uint32_t)npts * 32u * 8u > dyn_smem || nu > 32) return;  // the host sizes the launch; never stage out of bounds
-  for (int i = threadIdx.x; i < npts * 32; i += blockDim.x) acc[i] = 0;
+  if (nu > 32) return;
   if (threadIdx.x < 32) s_emax[threadIdx.x] = 0;
   __syncthreads();
-  const int gs_n = (int)fr.s_n * U, gs_a = (int)fr.s_t0 * U, gs_b = (int)fr.s_t1 * U;
-  // pass A: largest exponent of the ghost gradients of every item, per
-  // unknown; a warp takes one ghost row (p volumes along t0) at a time
+  const int gs_a = (int)fr.s_t0 * U;
+  // a warp takes one ghost row (p volumes along t0) at a time
   if (lane < nu) {
     int emax = 0;
     for (int mi = m0; mi < m1; ++mi) {
@@ -292,7 +280,50 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
     atomicMax(&s_emax[lane], emax);
   }
   __syncthreads();
-  const int E = lane < nu ? s_emax[lane] : 0;
+  if (threadIdx.x < nu)
+    reinterpret_cast<long long*>(g_coarse)[first.coarse_offset + t.u0 + threadIdx.x] = s_emax[threadIdx.x];
+}
+
+// ---------------------------------------------------------------------------
+// g_coarse = P^T g_fine, fixed point, for one group of items sharing a
+// coarse face array (finite-difference items, p a multiple of 3) and a chunk
+// of <= 32 unknowns.  One warp per coarse centre, lane = unknown.  Writes
+// every value of the group's coarse face array (zero where nothing reaches).
+// rn_lo / rn_hi: signed normal layers of the accumulator (the union of the
+// items' stencil regions).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kAdjThreads, 2)
+    interp_adjoint_fixed_kernel(const amr_transfer_item* __restrict__ items, const AdjointTile* __restrict__ tiles,
+                                const int32_t* __restrict__ group_ptr, const int32_t* __restrict__ group_items, int U,
+                                const double* __restrict__ g_fine, double* __restrict__ g_coarse) {
+  extern __shared__ double smem_raw[];
+  long long* acc = reinterpret_cast<long long*>(smem_raw);
+  const AdjointTile t = tiles[blockIdx.x];
+  const int m0 = group_ptr[t.index], m1 = group_ptr[t.index + 1];
+  const amr_transfer_item first = items[group_items[m0]];
+  const int p = first.patch_size, k = first.overlap;
+  const FaceFrame fr = face_frame(first.face, p, k);
+  const int64_t arr = fr.vols * U;
+  int rlo = 0, rhi = -1;  // union of the items' normal stencil ranges
+  for (int mi = m0; mi < m1; ++mi) {
+    IRange rn, ra, rb;
+    interp_region(p, k, items[group_items[mi]].order, 0, p, 0, p, rn, ra, rb);
+    rlo = min(rlo, rn.lo);
+    rhi = max(rhi, rn.hi);
+  }
+  const int NJ = rhi - rlo + 1, npts = NJ * p * p;
+  const int nu = t.nu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t dyn_smem;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
+  if ((uint32_t)npts * 32u * 8u > dyn_smem || nu > 32) return;  // the host sizes the launch; never stage out of bounds
+  for (int i = threadIdx.x; i < npts * 32; i += blockDim.x) acc[i] = 0;
+  __syncthreads();
+  const int gs_n = (int)fr.s_n * U, gs_a = (int)fr.s_t0 * U, gs_b = (int)fr.s_t1 * U;
+  // the largest biased exponent of the group's ghost gradients for this
+  // lane's unknown, left by adjoint_emax_kernel in the first volume of the
+  // group's coarse face array (read before this CTA writes it)
+  const int E = lane < nu ? (int)reinterpret_cast<const long long*>(g_coarse)[first.coarse_offset + t.u0 + lane] : 0;
   const bool finite = E < 2047;
   const int s = kAdjBits - (max(E, 62) - 1022);  // |g| < 2^(E - 1022) -> |n| < 2^44
   // pass B: per item and coarse centre (one warp), the transposed operator
