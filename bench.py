@@ -376,7 +376,8 @@ def main():
     restrict_gbs = info["restrict_bytes"] / (t_restrict * 1e-3) / 1e9
     ikern = {B.PREC_FIXED: "interp_fixed_kernel", B.PREC_SPLIT: "interp_kernel_split",
              B.PREC_FP64: "interp_kernel_fp64"}[prec]
-    rkern = "restrict_kernel_split" if prec == B.PREC_SPLIT else "restrict_kernel_fp64"
+    rkern = {B.PREC_FIXED: "restrict_kernel_fixed", B.PREC_SPLIT: "restrict_kernel_split",
+             B.PREC_FP64: "restrict_kernel_fp64"}[prec]
     roofline = {"bound": "hbm", "kernel": ikern, "achieved": interp_gbs, "peak": hbm_peak,
                 "unit": "GB/s", "frac": interp_gbs / hbm_peak,
                 "traffic": profiled_traffic(ikern, args.faces),
@@ -389,7 +390,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {B.PREC_FIXED: "int64 interpolation, f64 restriction", B.PREC_SPLIT: "f64 base / f32 increment",
+            "dtype": {B.PREC_FIXED: "int64 interpolation, f64 + int64 restriction", B.PREC_SPLIT: "f64 base / f32 increment",
                       B.PREC_FP64: "f64"}[prec],
             "data": "synthetic",
             "config": {"workload": f"uniform batch: {args.faces} hanging faces per GPU, p={P}, k={K}, U={U}, "

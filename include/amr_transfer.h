@@ -91,8 +91,10 @@ typedef enum {
      holding a NaN or an infinity makes every other child of that unknown in
      the tile NaN; results beyond the float64 range become infinite, below
      its normal range +0; regions whose largest magnitude is below 2^-960
-     are quantized on the grid of 2^-960 instead.  Restriction and the
-     least-squares scheme use the float64 kernels. */
+     are quantized on the grid of 2^-960 instead.  Restriction: float64
+     for half the coarse columns, exact integer sums on a 62-bit grid per
+     column for the other half (float64 accuracy or better).  The
+     least-squares scheme uses the float64 kernels. */
   AMR_PREC_FIXED = 2
 } amr_precision;
 

@@ -52,6 +52,8 @@ amr_status upload_tables(int device) {
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw_hi, t.rw_hi, sizeof t.rw_hi));
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw_lo, t.rw_lo, sizeof t.rw_lo));
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_fxw, t.fxw, sizeof t.fxw));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_rwx, t.rwx, sizeof t.rwx));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw_den, t.rw_den, sizeof t.rw_den));
   g_tables_ready[device] = 1;
   return AMR_OK;
 }
@@ -585,6 +587,9 @@ amr_status amr_transfer_plan_restrict(amr_transfer_plan* p, const double* fine, 
   if (p->n_rtiles == 0) return AMR_OK;
   if (p->precision == AMR_PREC_SPLIT)
     amr::restrict_kernel<amr::kRestrictSplit><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(
+        p->items_d, p->rtiles_d, p->U, fine, coarse);
+  else if (p->precision == AMR_PREC_FIXED)
+    amr::restrict_kernel<amr::kRestrictFixed><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(
         p->items_d, p->rtiles_d, p->U, fine, coarse);
   else
     amr::restrict_kernel<amr::kRestrictF64><<<p->n_rtiles, p->tuning.restrict_threads, 0, s>>>(

@@ -111,6 +111,7 @@ Tables make_tables() {
         stencil_window(k - 1, -k, k - 1, pure_exactness(order), s0, L);
         const int pos = k - 1 - s0;
         const int e = 3 * j + 2 - k;
+        Q row[5];
         for (int i = 0; i < 5; ++i) {
           Q w(0);
           if (i < L) {
@@ -125,7 +126,29 @@ Tables make_tables() {
           t.rw[idx] = w.to_double();
           t.rw_hi[idx] = (float)t.rw[idx];
           t.rw_lo[idx] = (float)(t.rw[idx] - (double)t.rw_hi[idx]);
+          row[i] = w;
         }
+        // exact integer form: D = lcm of the row's denominators = 2^a 3^b
+        int64_t D = 1;
+        for (int i = 0; i < 5; ++i) D = std::lcm(D, row[i].d);
+        int a2 = 0, b3 = 0;
+        int64_t rest = D;
+        while (rest % 2 == 0) { rest /= 2; ++a2; }
+        while (rest % 3 == 0) { rest /= 3; ++b3; }
+        if (rest != 1 || b3 > 1 || a2 > 15) {
+          std::fprintf(stderr, "amr_transfer: restriction weight denominator %lld (order %d, k %d, j %d)\n",
+                       (long long)D, order, k, j);
+          std::abort();
+        }
+        for (int i = 0; i < 5; ++i) {
+          const Q n = row[i] * Q(D);
+          if (n.d != 1 || n.n >= (1 << 15) || n.n <= -(1 << 15)) {  // the kernel's sums assume |W| < 2^15
+            std::fprintf(stderr, "amr_transfer: restriction numerator out of range (order %d, k %d, j %d)\n", order, k, j);
+            std::abort();
+          }
+          t.rwx[rw_index(order, k, j) + i] = (int32_t)n.n;
+        }
+        t.rw_den[rw_index(order, k, j) / 5] = a2 | b3 << 4;
         // least-squares scheme: the fit along the same window through the
         // expansion value (the base takes 1 - sum of the others)
         std::vector<std::array<int, 3>> rel;

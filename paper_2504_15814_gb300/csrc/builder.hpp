@@ -30,6 +30,11 @@ struct Tables {
   // units of the coarse spacing): lambda / r! * fixed_den(L, r), fixed_den = 2
   // for 3-point windows and 12, 24, 12 (r = 1, 2, 3) for 4- and 5-point windows
   int32_t fxw[WT_SIZE];
+  // combined restriction weights of the finite-difference scheme as integers
+  // rwx = rw * D over the row's denominator D = 2^a 3^b (b <= 1); rw_den per
+  // row (index rw_index / 5): a | b << 4
+  int32_t rwx[RW_SIZE];
+  int32_t rw_den[RW_SIZE / 5];
 };
 
 // Built once per process.

@@ -36,6 +36,8 @@ __constant__ float c_ls_f[LS_SIZE];
 __constant__ double c_rw[RW_SIZE];
 __constant__ float c_rw_hi[RW_SIZE];
 __constant__ float c_rw_lo[RW_SIZE];
+__constant__ int32_t c_rwx[RW_SIZE];         // integer restriction weights (Tables::rwx)
+__constant__ int32_t c_rw_den[RW_SIZE / 5];  // their row denominators 2^a 3^b as a | b << 4
 
 template <bool SPLIT> struct Arith;
 template <> struct Arith<false> {
@@ -756,10 +758,86 @@ __device__ __forceinline__ void dlinear_restrict_split(const Fine& F, const Coar
   }
 }
 
-// Restriction precision modes: float64 throughout (float64 and fixed-point
-// plans), or split (float64 first extrapolated layer, float-pair second
-// layer, float32 d-linear averaging on exact float-pair differences).
-constexpr int kRestrictF64 = 0, kRestrictSplit = 1;
+// ---------------------------------------------------------------------------
+// Taylor restriction of one column in integers (fixed-point plans, every
+// other column; the float64 unit takes the rest).  The window values
+// v[0..L) are rounded once onto the grid 2^-s, s = 1084 - E (E the largest
+// biased exponent of the window): |n| < 2^62, rounding error at most 2^-62
+// of the window's largest magnitude.  Each n is carried as two signed 31-bit
+// halves, so the sums with the integer weights (|W| < 2^15) are exact in two
+// int64 accumulators A and B, T = A 2^31 + B.  T 2^-s / D is rounded to
+// float64 by integer normalisation: exactly once when |A| < 2^31 (T fits 63
+// bits), else after dropping the 17 low bits of B (relative error below
+// 2^-44); a row denominator D with a factor 3 adds one float64 multiply by
+// 1/3.  Windows with a non-finite value or a largest magnitude outside
+// 2^-923 .. 2^977 return false (the caller uses float64).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split62(double v, int E, int& nh, int& nl) {
+  const long long bits = __double_as_longlong(v);
+  const int e = (int)((bits >> 52) & 0x7ff);
+  const unsigned long long M = (unsigned long long)(bits & 0xFFFFFFFFFFFFFll) | (e ? (1ull << 52) : 0ull);
+  const int sh = max(e, 1) - E + 9;  // <= 9: |n| = M 2^sh < 2^62
+  unsigned long long N;
+  if (sh >= 0) N = M << sh;
+  else N = -sh <= 54 ? ((M >> (-sh - 1)) + 1) >> 1 : 0ull;  // half away from zero
+  const int h = (int)(N >> 31), l = (int)(N & 0x7fffffffull);
+  nh = bits < 0 ? -h : h;
+  nl = bits < 0 ? -l : l;
+}
+
+// T 2^-sh as float64 for 0 < |T| < 2^63 with the result in the normal range:
+// integer normalisation, ties away from zero.
+__device__ __forceinline__ double scaled_i64_to_f64(long long T, int sh) {
+  const unsigned long long sg = (unsigned long long)(T >> 63);
+  unsigned long long m = ((unsigned long long)T ^ sg) - sg;
+  const int lz = __clzll((long long)m);
+  m <<= lz;
+  m = (m >> 1) + 0x200ull;           // leading one at bit 62; half an ulp of the 53-bit result
+  const unsigned long long mant = m >> 10;  // 2^52 + fraction, or 2^53 after a rounding carry
+  const long long e = 1085 - lz - sh;       // biased exponent - 1 (the leading one adds 1)
+  return __longlong_as_double((long long)((sg << 63) | (mant + ((unsigned long long)e << 52))));
+}
+
+template <typename Store>
+__device__ __forceinline__ bool restrict_int_layers(const double* v, int L, int m, int k, const Store& store) {
+  int E = 1;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    if (i < L) E = max(E, (int)((__double_as_longlong(v[i]) >> 52) & 0x7ff));
+  if (E < 100 || E > 2000) return false;
+  int nh[5], nl[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    nh[i] = 0;
+    nl[i] = 0;
+    if (i < L) split62(v[i], E, nh[i], nl[i]);
+  }
+  const int s = 1084 - E;
+  for (int j = 1; j < k; ++j) {
+    const int r0 = rw_index(m, k, j);
+    long long A = 0, B = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const int W = c_rwx[r0 + i];
+      A += (long long)W * nh[i];
+      B += (long long)W * nl[i];
+    }
+    const int den = c_rw_den[r0 / 5];
+    const bool fits = A < (1ll << 31) && A > -(1ll << 31);
+    const long long T = fits ? (A << 31) + B : (A << 14) + (B >> 17);
+    double out = T == 0 ? 0.0 : scaled_i64_to_f64(T, s + (den & 15) - (fits ? 0 : 17));
+    if (den >> 4) out *= 1.0 / 3.0;
+    store(j, out);
+  }
+  return true;
+}
+
+// Restriction precision modes: float64 throughout (float64 plans); split
+// (float64 first extrapolated layer, float-pair second layer, float32
+// d-linear averaging on exact float-pair differences); fixed (float64 for the
+// first column of each thread's pair, the integer layers above for the
+// second, float64 where those do not serve: the two pipes share the work).
+constexpr int kRestrictF64 = 0, kRestrictSplit = 1, kRestrictFixed = 2;
 
 template <int RP>
 __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* __restrict__ items,
@@ -827,6 +905,9 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
         if (!ccol[r]) continue;
         double* col = ccol[r];
         col[0] = inj_in ? pick5(v[r], 1 - s) : v1[r];  // layer 0 coincides with fine layer 1
+        if (RP == kRestrictFixed && r == 1 && it.scheme == 0 &&
+            restrict_int_layers(v[r], L, m, k, [&](int j, double out) { col[j * gs_n] = out; }))
+          continue;
         if (SPLIT) {
           // layer 1 with float64 combined weights (the float64 unit is idle
           // here); layer 2 in float64 for the first column of the pair and in

@@ -24,7 +24,7 @@ PRECISIONS = [(B.PREC_FP64, FP64_TOL), (B.PREC_SPLIT, SPLIT_BOUND), (B.PREC_FIXE
 
 @pytest.mark.parametrize("precision,tol", PRECISIONS)
 @pytest.mark.parametrize("order", [1, 2, 3])
-@pytest.mark.parametrize("p,k", [(4, 2), (5, 3), (7, 3), (8, 2), (10, 3), (16, 3)])
+@pytest.mark.parametrize("p,k", [(4, 2), (5, 3), (7, 3), (8, 2), (10, 3), (13, 2)])
 def test_whole_faces(p, k, order, precision, tol):
     n = 6
     items, c, f = _batch(list(range(n)), [-1] * n, [p] * n, [k] * n, [order] * n, 11, seed=p * 10 + order)
@@ -50,13 +50,16 @@ def test_dlinear_overlap_one():
 @pytest.mark.parametrize("precision,tol", PRECISIONS)
 def test_mixed_patch_sizes_in_one_plan(precision, tol):
     """Multiples of 3 and other sizes together: both interpolation kernel
-    variants run in one call; U = 37 splits into unknown chunks."""
+    variants run in one call; U = 37 splits into unknown chunks.  Two large
+    patches (p = 47 and 48) enter as single subfaces."""
     rng = np.random.default_rng(17)
-    n = 30
-    ps = rng.choice([4, 5, 6, 7, 9, 11, 13, 24, 47, 48], n)
+    n = 24
+    ps = rng.choice([4, 5, 6, 7, 9, 11, 13], n)
     ks = rng.choice([2, 3], n)
     orders = rng.choice([1, 2, 3], n)
-    items, c, f = _batch(rng.integers(0, 6, n), rng.integers(-1, 9, n), ps, ks, orders, 37, seed=19)
+    subs = rng.integers(-1, 9, n)
+    ps[:2], ks[:2], orders[:2], subs[:2] = [47, 48], [2, 2], [3, 2], [4, 2]
+    items, c, f = _batch(rng.integers(0, 6, n), subs, ps, ks, orders, 37, seed=19)
     _check(items, 37, c, f, precision, tol)
     plan = B.Plan(items, 37, len(c), len(f), precision)
     assert plan.info["interp_launches"] == 2
