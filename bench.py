@@ -110,15 +110,26 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash():
-    """sha256 of the CUDA/C++ sources of the library (sorted by name)."""
+# CUDA sources each profiled kernel is compiled from (its own file and the
+# headers it includes)
+KERNEL_SOURCES = {
+    "interp_fixed_kernel": ["fixed_kernels.cuh", "transfer_kernels.cuh", "amr_common.cuh", "split_arith.cuh"],
+    "restrict_kernel_fixed": ["restrict_kernels.cuh", "transfer_kernels.cuh", "amr_common.cuh", "split_arith.cuh"],
+    "restrict_kernel_fp64": ["restrict_kernels.cuh", "transfer_kernels.cuh", "amr_common.cuh", "split_arith.cuh"],
+    "restrict_kernel_split": ["restrict_kernels.cuh", "transfer_kernels.cuh", "amr_common.cuh", "split_arith.cuh"],
+}
+
+
+def kernel_source_hash(kernel=None):
+    """sha256 of the CUDA sources a kernel is compiled from (sorted by name;
+    every CUDA/C++ source of the library for a kernel not listed)."""
     import hashlib
     d = os.path.join(ROOT, "paper_2504_15814_gb300", "csrc")
+    names = KERNEL_SOURCES.get(kernel) or [n for n in os.listdir(d) if n.endswith((".cu", ".cuh", ".cpp", ".hpp"))]
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".cpp", ".hpp")):
-            with open(os.path.join(d, name), "rb") as fh:
-                h.update(name.encode() + b"\0" + fh.read())
+    for name in sorted(names):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
     return h.hexdigest()
 
 
@@ -136,7 +147,7 @@ def profiled_traffic(kernel, faces):
         if line.startswith("- ") and ": " in line:
             key, val = line[2:].split(": ", 1)
             fields[key.strip()] = val.strip().strip("`")
-    if fields.get("source_sha256") != kernel_source_hash():
+    if fields.get("source_sha256") != kernel_source_hash(kernel):
         return None
     try:
         return float(fields["dram_bytes_per_face"]) * faces

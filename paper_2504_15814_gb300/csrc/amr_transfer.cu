@@ -13,6 +13,7 @@
 #include "adjoint_kernels.cuh"
 #include "csr_kernels.cuh"
 #include "transfer_kernels.cuh"
+#include "restrict_kernels.cuh"
 #include "fixed_kernels.cuh"
 #include "fixed_adjoint.cuh"
 
