@@ -55,6 +55,8 @@ amr_status upload_tables(int device) {
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_fxw, t.fxw, sizeof t.fxw));
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_rwx, t.rwx, sizeof t.rwx));
   AMR_CUDA(cudaMemcpyToSymbol(amr::c_rw_den, t.rw_den, sizeof t.rw_den));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_lsx, t.lsx, sizeof t.lsx));
+  AMR_CUDA(cudaMemcpyToSymbol(amr::c_ls_den, t.ls_den, sizeof t.ls_den));
   g_tables_ready[device] = 1;
   return AMR_OK;
 }

@@ -94,11 +94,27 @@ Tables make_tables() {
     for (int i : layers) { Q dx = Q(2 * i + 1, 6) - mean; sxx = sxx + dx * dx; }
     for (int j = 0; j < k; ++j) {
       const Q xc(2 * j + 1, 2);
+      Q row[kMaxOverlap];
       for (int s = 0; s < nl; ++s) {
         const Q w = Q(1, nl) + (Q(2 * layers[s] + 1, 6) - mean) * (xc - mean) / sxx;
         t.ls[ls_index(k, j, s)] = w.to_double();
         t.ls_f[ls_index(k, j, s)] = (float)w.to_double();
+        row[s] = w / Q(9);  // applied to the sum of the 3 x 3 tangential values
       }
+      // exact integer form over D = 2^a 3^b (b <= 3), else marked unusable
+      int64_t D = 1;
+      for (int s = 0; s < nl; ++s) D = std::lcm(D, row[s].d);
+      int a2 = 0, b3 = 0;
+      int64_t rest = D;
+      while (rest % 2 == 0) { rest /= 2; ++a2; }
+      while (rest % 3 == 0) { rest /= 3; ++b3; }
+      bool ok = rest == 1 && b3 <= 3 && a2 <= 15;
+      for (int s = 0; s < nl && ok; ++s) {
+        const Q n = row[s] * Q(D);
+        ok = n.d == 1 && n.n < (1 << 10) && n.n > -(1 << 10);
+        if (ok) t.lsx[ls_index(k, j, s)] = (int32_t)n.n;
+      }
+      t.ls_den[(k - 1) * kMaxOverlap + j] = ok ? (a2 | b3 << 4 | 1 << 8) : 0;
     }
   }
   // Combined restriction weights (exact): W[i] = [s + i == k - 1] +

@@ -35,6 +35,11 @@ struct Tables {
   // row (index rw_index / 5): a | b << 4
   int32_t rwx[RW_SIZE];
   int32_t rw_den[RW_SIZE / 5];
+  // d-linear restriction: least-squares line weights / 9 as integers over a
+  // per-row denominator D = 2^a 3^b; ls_den[(k - 1) * kMaxOverlap + j] =
+  // a | b << 4 | 1 << 8 (0: no such form, float64 only)
+  int32_t lsx[LS_SIZE];
+  int32_t ls_den[kMaxOverlap * kMaxOverlap];
 };
 
 // Built once per process.

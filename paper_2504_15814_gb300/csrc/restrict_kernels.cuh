@@ -12,6 +12,8 @@ namespace amr {
 
 __constant__ int32_t c_rwx[RW_SIZE];         // integer restriction weights (Tables::rwx)
 __constant__ int32_t c_rw_den[RW_SIZE / 5];  // their row denominators 2^a 3^b as a | b << 4
+__constant__ int32_t c_lsx[LS_SIZE];         // d-linear line weights / 9 as integers (Tables::lsx)
+__constant__ int32_t c_ls_den[kMaxOverlap * kMaxOverlap];  // a | b << 4 | usable << 8 per (k, j)
 
 // ---------------------------------------------------------------------------
 // Restriction tasks: one coarse halo column (a, b), one unknown.  F(i, da, db)
@@ -201,11 +203,67 @@ __device__ __forceinline__ bool restrict_int_layers(const double* v, int L, int 
   return true;
 }
 
+// d-linear restriction of one column in integers (fixed-point plans, half
+// the columns): the 9 nl fine values are rounded once onto the grid 2^-s of
+// the column's largest magnitude (s = 1084 - E, |n| < 2^62, 31-bit halves as
+// above), the 3 x 3 tangential sums of each fine layer are exact, and the
+// least-squares line weights / 9 are integers over D = 2^a 3^b, so each halo
+// value is one integer normalisation (plus a multiply by 3^-b).  Overlaps 4
+// and 5 (denominators with a 5), windows with a non-finite value or a
+// largest magnitude outside 2^-923 .. 2^977 return false.
+template <typename Fine, typename Coarse>
+__device__ __forceinline__ bool dlinear_restrict_int(const Fine& F, const Coarse& C, int k) {
+  if (k > 3) return false;
+  for (int j = 0; j < k; ++j)
+    if (!((c_ls_den[(k - 1) * kMaxOverlap + j] >> 8) & 1)) return false;
+  const int nl = k == 1 ? 2 : k;
+  int E = 1;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl)
+    if (sl < nl) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q)
+        E = max(E, (int)((__double_as_longlong(F(k == 1 ? sl - 1 : sl, q % 3 - 1, q / 3 - 1)) >> 52) & 0x7ff));
+    }
+  if (E < 100 || E > 2000) return false;
+  long long Sh[3] = {0, 0, 0}, Sl[3] = {0, 0, 0};
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl)
+    if (sl < nl) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        int nh, nlo;
+        split62(F(k == 1 ? sl - 1 : sl, q % 3 - 1, q / 3 - 1), E, nh, nlo);
+        Sh[sl] += nh;
+        Sl[sl] += nlo;
+      }
+    }
+  const int s = 1084 - E;
+  for (int j = 0; j < k; ++j) {
+    const int den = c_ls_den[(k - 1) * kMaxOverlap + j];
+    long long A = 0, B = 0;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl)
+      if (sl < nl) {
+        const long long W = c_lsx[ls_index(k, j, sl)];
+        A += W * Sh[sl];
+        B += W * Sl[sl];
+      }
+    const bool fits = A < (1ll << 31) && A > -(1ll << 31);
+    const long long T = fits ? (A << 31) + B : (A << 14) + (B >> 17);
+    double out = T == 0 ? 0.0 : scaled_i64_to_f64(T, s + (den & 15) - (fits ? 0 : 17));
+    const int b3 = (den >> 4) & 15;
+    if (b3) out *= b3 == 1 ? 1.0 / 3.0 : (b3 == 2 ? 1.0 / 9.0 : 1.0 / 27.0);
+    C(j, out);
+  }
+  return true;
+}
+
 // Restriction precision modes: float64 throughout (float64 plans); split
 // (float64 first extrapolated layer, float-pair second layer, float32
-// d-linear averaging on exact float-pair differences); fixed (float64 for the
-// first column of each thread's pair, the integer layers above for the
-// second, float64 where those do not serve: the two pipes share the work).
+// d-linear averaging on exact float-pair differences); fixed (float64 for
+// half the columns, the integer paths above for the other half, float64
+// where those do not serve: the two pipes share the work).
 constexpr int kRestrictF64 = 0, kRestrictSplit = 1, kRestrictFixed = 2;
 
 template <int RP>
@@ -316,7 +374,8 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
       }
     }
   } else {
-    for (int e = threadIdx.x; e < ntask; e += blockDim.x, c.advance(nu, t.na, t.nb)) {
+    int round = threadIdx.x >> 5;  // fixed-point plans: warps alternate float64 and integer columns
+    for (int e = threadIdx.x; e < ntask; e += blockDim.x, c.advance(nu, t.na, t.nb), ++round) {
       const double* fcol;
       double* ccol;
       int q0, q1;
@@ -327,6 +386,7 @@ __global__ void __launch_bounds__(256) restrict_kernel(const amr_transfer_item* 
       const int ga = (q0 == 0 || q0 == p - 1) ? 0 : gs_a, gb = (q1 == 0 || q1 == p - 1) ? 0 : gs_b;
       auto F = [&](int i, int da, int db) -> double { return __ldg(fcol + i * gs_n + da * ga + db * gb); };
       auto C = [&](int j, double v) { ccol[j * gs_n] = v; };
+      if (RP == kRestrictFixed && (round & 1) && dlinear_restrict_int(F, C, k)) continue;
       if (SPLIT) dlinear_restrict_split(F, C, k);
       else dlinear_restrict_f64(F, C, k);
     }

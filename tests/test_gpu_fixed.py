@@ -256,13 +256,14 @@ def test_full_size_puncture_batch(precision, tol):
     plan.close()
 
 
-@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_fixed_restriction_windows(order):
-    """Restriction of fixed-point plans (float64 arithmetic) on adversarial
-    windows: unknowns scaled to 2^-925 .. 2^978, values spread over twenty
-    decades inside one window, a NaN in one fine face array; every unknown
-    matches the oracle at the float64 tolerance (NaN where the oracle gives
-    NaN)."""
+    """Restriction of fixed-point plans (float64 columns and exact integer
+    columns side by side) on adversarial windows: unknowns scaled to both
+    sides of both ends of the integer path's range (2^-923 .. 2^977), values
+    spread over twenty decades inside one window, a NaN in one fine face
+    array; every unknown matches the oracle at the float64 tolerance (NaN
+    where the oracle gives NaN)."""
     U = 8
     items, c, f = _faces(U, order, 30 + order, p=9)
     rng = np.random.default_rng(77 + order)

@@ -100,10 +100,11 @@ def test_overlaps_four_and_five(k, order, precision, tol):
     _check(items, 11, c, f, precision, tol)
 
 
-def test_dlinear_overlap_one():
+@pytest.mark.parametrize("precision,tol", PRECISIONS)
+def test_dlinear_overlap_one(precision, tol):
     n = 6
     items, c, f = _batch(list(range(6)), [-1] * n, [6] * n, [1] * n, [1] * n, 3, seed=5)
-    _check(items, 3, c, f, B.PREC_FP64, FP64_TOL)
+    _check(items, 3, c, f, precision, tol)
 
 
 def test_mixed_batch_and_large_patches():
