@@ -207,6 +207,29 @@ amr_status amr_transfer_plan_interpolate_increments(amr_transfer_plan* plan, con
 amr_status amr_transfer_plan_apply_increments(amr_transfer_plan* plan, const double* coarse,
                                               const float* increments, double* fine, void* cuda_stream);
 
+/* Diagonal (edge and vertex) ghost volumes.  The paper's transfer carries no
+ * diagonal data (Sec. 2: only the face arrays of a hanging face); a fine patch
+ * whose stencils reach across its edges also needs ghost volumes beyond its
+ * subface.  This call fills, for every fine face array of every item, the
+ * ghost half widened by k volumes on each tangential side, by the same rule as
+ * interpolate: each volume is reconstructed about its nearest coarse centre of
+ * the item's coarse face array (the face's edge centre for volumes past the
+ * edge, at offsets beyond one fine spacing) with that centre's derivative
+ * stencils and Taylor's formula, or by the d-linear tensor product with linear
+ * extrapolation past the edge.  Inside the subface the values equal the
+ * ordinary ghost values (to rounding).  Float64 arithmetic in every precision
+ * mode.  Layout of diag: item i starts at the sum over earlier items of
+ * (number of fine face arrays) * k * (p + 2k)^2 * U; inside an item, element
+ * ((((s * k + g) * W + q1 + k) * W + q0 + k) * U + u with W = p + 2k, fine
+ * face array s, ghost layer g (0 next to the interface), tangential local
+ * indices q1 (t1) and q0 (t0) in [-k, p + k), unknown u.  diag_elems is the
+ * caller's buffer size; smaller than that sum: AMR_ERR_INVALID_ARGUMENT.
+ * Overlaps 1..3 and finite-difference Taylor or d-linear items only
+ * (AMR_ERR_UNSUPPORTED otherwise).  The first call on a plan builds its tile
+ * table (a synchronous upload): make it before capturing a stream. */
+amr_status amr_transfer_plan_interpolate_diagonal(amr_transfer_plan* plan, const double* coarse, double* diag,
+                                                  int64_t diag_elems, void* cuda_stream);
+
 /* Plan facts used to report throughput. */
 typedef struct {
   int64_t num_items;

@@ -40,6 +40,16 @@ class Desc(ctypes.Structure):
                 ("items", ctypes.c_void_p), ("coarse_elems", ctypes.c_int64), ("fine_elems", ctypes.c_int64)]
 
 
+def diagonal_elems(items, num_unknowns):
+    """float64 values of the diagonal-halo buffer: per item, per fine face
+    array, k ghost layers of (p + 2k)^2 volumes of U unknowns."""
+    total = 0
+    for it in items:
+        p, k = int(it["patch_size"]), int(it["overlap"])
+        total += (9 if int(it["subface"]) < 0 else 1) * k * (p + 2 * k) ** 2 * int(num_unknowns)
+    return total
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [("num_items", ctypes.c_int64), ("interp_outputs", ctypes.c_int64),
                 ("restrict_outputs", ctypes.c_int64), ("interp_bytes", ctypes.c_int64),
@@ -62,6 +72,7 @@ ENTRY_POINTS = {
     "amr_transfer_plan_get_info": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "amr_transfer_plan_interpolate_increments": ([ctypes.c_void_p] * 4, ctypes.c_int),
     "amr_transfer_plan_apply_increments": ([ctypes.c_void_p] * 5, ctypes.c_int),
+    "amr_transfer_plan_interpolate_diagonal": ([ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "amr_transfer_plan_get_tuning": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "amr_transfer_plan_set_tuning": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "amr_transfer_plan_autotune": ([ctypes.c_void_p] * 6, ctypes.c_int),
@@ -149,6 +160,7 @@ class Plan:
         self.coarse_elems = int(coarse_elems)
         self.fine_elems = int(fine_elems)
         self.precision = int(precision)
+        self.diagonal_elems = diagonal_elems(items, num_unknowns)
 
     def _sized(self, x, n, name):
         if not isinstance(x, int) and x is not None:
@@ -195,6 +207,15 @@ class Plan:
             self._fptr(increments, self.info["increment_elems"], "increments"),
             self._sized(fine, self.fine_elems, "fine"), _stream(stream)), "apply_increments")
         return fine
+
+    def interpolate_diagonal(self, coarse, diag, stream=None):
+        """Widened ghost boxes of every subface (edge and vertex halos), float64;
+        layout in amr_transfer_plan_interpolate_diagonal."""
+        _check(lib().amr_transfer_plan_interpolate_diagonal(
+            self._handle, self._sized(coarse, self.coarse_elems, "coarse"),
+            self._sized(diag, self.diagonal_elems, "diag"), self.diagonal_elems, _stream(stream)),
+            "interpolate_diagonal")
+        return diag
 
     def interpolate_adjoint(self, g_fine, g_coarse, stream=None):
         _check(lib().amr_transfer_plan_interpolate_adjoint(

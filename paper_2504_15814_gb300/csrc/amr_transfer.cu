@@ -14,6 +14,7 @@
 #include "csr_kernels.cuh"
 #include "transfer_kernels.cuh"
 #include "restrict_kernels.cuh"
+#include "diagonal_kernels.cuh"
 #include "fixed_kernels.cuh"
 #include "fixed_adjoint.cuh"
 
@@ -152,6 +153,12 @@ struct amr_transfer_plan {
   int32_t *cls_pt_rows_d = nullptr, *cls_rt_rows_d = nullptr, *pt_row_ptr_d = nullptr, *rt_row_ptr_d = nullptr;
   uint32_t *pt_col_d = nullptr, *rt_col_d = nullptr;
   double *pt_val_d = nullptr, *rt_val_d = nullptr;
+  // diagonal-halo tables, built on the first such call
+  bool diag_ready = false;
+  int n_diag_tiles = 0;
+  int64_t diag_elems = 0;
+  amr::AdjointTile* diag_tiles_d = nullptr;
+  int64_t* diag_off_d = nullptr;
 };
 
 static void drop_graph(amr_transfer_plan* p) {
@@ -165,7 +172,7 @@ static void free_plan(amr_transfer_plan* p) {
   void* csr[] = {p->cpt_d, p->crt_d, p->pf_row_d, p->rf_row_d, p->pf_col_d, p->rf_col_d, p->pf_out_d,
                  p->rf_out_d, p->pf_base_d, p->rf_base_d, p->pf_val_d, p->rf_val_d, p->pf_valf_d};
   for (void* q : csr) cudaFree(q);
-  void* ls[] = {p->ls_wf_d, p->ls_wd_d, p->ls_off_d};
+  void* ls[] = {p->ls_wf_d, p->ls_wd_d, p->ls_off_d, p->diag_tiles_d, p->diag_off_d};
   for (void* q : ls) cudaFree(q);
   void* ptrs[] = {p->items_d, p->itiles_d, p->rtiles_d, p->incr_off_d, p->incr_tiles_d, p->pt_tiles_d, p->rt_tiles_d,
                   p->fx_pt_tiles_d, p->rtt_tiles_d, p->group_ptr_d,
@@ -264,6 +271,37 @@ static amr_status ensure_adjoint(amr_transfer_plan* p) {
   p->n_pt_tiles = (int)ab.pt_tiles.size();
   p->n_rt_tiles = (int)ab.rt_tiles.size();
   p->adj_ready = true;
+  return AMR_OK;
+}
+
+// Tables of the diagonal-halo call: one tile per fine face array and chunk of
+// <= 128 unknowns, and the element offset of each item's widened boxes.
+static amr_status ensure_diagonal(amr_transfer_plan* p) {
+  if (p->diag_ready) return AMR_OK;
+  std::vector<amr::AdjointTile> tiles;
+  std::vector<int64_t> off;
+  int64_t total = 0;
+  for (size_t i = 0; i < p->items_h.size(); ++i) {
+    const amr_transfer_item& x = p->items_h[i];
+    if (x.overlap > 3 || (x.order >= 2 && x.scheme != 0)) return AMR_ERR_UNSUPPORTED;
+    const int nsub = x.subface < 0 ? 9 : 1;
+    const int64_t W = x.patch_size + 2LL * x.overlap;
+    off.push_back(total);
+    total += nsub * x.overlap * W * W * p->U;
+    for (int sl = 0; sl < nsub; ++sl)
+      for (int64_t u0 = 0; u0 < p->U; u0 += 128)
+        tiles.push_back({(int32_t)i, (int16_t)sl, 0, (int16_t)u0, (int16_t)std::min<int64_t>(128, p->U - u0)});
+  }
+  amr_status st;
+  if ((st = upload(tiles, &p->diag_tiles_d)) != AMR_OK) return st;
+  if ((st = upload(off, &p->diag_off_d)) != AMR_OK) {
+    cudaFree(p->diag_tiles_d);
+    p->diag_tiles_d = nullptr;
+    return st;
+  }
+  p->n_diag_tiles = (int)tiles.size();
+  p->diag_elems = total;
+  p->diag_ready = true;
   return AMR_OK;
 }
 
@@ -622,6 +660,19 @@ amr_status amr_transfer_plan_interpolate_adjoint(amr_transfer_plan* p, const dou
         p->pt_row_ptr_d, p->pt_col_d, p->pt_val_d, p->U, g_fine, g_coarse);
     AMR_CUDA(cudaGetLastError());
   }
+  return AMR_OK;
+}
+
+amr_status amr_transfer_plan_interpolate_diagonal(amr_transfer_plan* p, const double* coarse, double* diag,
+                                                  int64_t diag_elems, void* stream) {
+  amr_status st = check_call(p, coarse, p ? p->coarse_elems : 0, diag, diag_elems);
+  if (st != AMR_OK) return st;
+  if ((st = ensure_diagonal(p)) != AMR_OK) return st;
+  if (diag_elems < p->diag_elems) return AMR_ERR_INVALID_ARGUMENT;
+  if (p->n_diag_tiles == 0) return AMR_OK;
+  amr::interp_diagonal_kernel<<<p->n_diag_tiles, 256, 0, (cudaStream_t)stream>>>(
+      p->items_d, p->diag_tiles_d, p->U, p->diag_off_d, coarse, diag);
+  AMR_CUDA(cudaGetLastError());
   return AMR_OK;
 }
 

@@ -120,10 +120,9 @@ __device__ __forceinline__ void taylor_children(const T (&C)[M + 1][M + 1][M + 1
 // of h; fine signed layer -1-ii for cl = -1) and tangential offsets e0, e1 in
 // {-1, 0, 1}.
 // ---------------------------------------------------------------------------
-template <int M, typename T, typename Diff, typename Emit>
-__device__ __forceinline__ void taylor_interp_core(const Diff& D, const Emit& emit, const T* __restrict__ wt,
-                                                   int k, int p, int a, int b, T c000, int cl = -1,
-                                                   int kk = 3) {
+template <int M, typename T, typename Diff>
+__device__ __forceinline__ void taylor_interp_coeffs(const Diff& D, const T* __restrict__ wt, int k, int p, int a,
+                                                     int b, T c000, int cl, T (&C)[M + 1][M + 1][M + 1]) {
   const int c[3] = {cl, a, b};
   const int lo[3] = {-k, 0, 0};
   const int hi[3] = {k - 1, p - 1, p - 1};
@@ -135,7 +134,6 @@ __device__ __forceinline__ void taylor_interp_core(const Diff& D, const Emit& em
   }
   auto W = [&](int L, int pos, int r) -> const T* { return wt + wt_offset(L) + (pos * 3 + r - 1) * L; };
 
-  T C[M + 1][M + 1][M + 1];
 #pragma unroll
   for (int x = 0; x <= M; ++x)
 #pragma unroll
@@ -235,6 +233,16 @@ __device__ __forceinline__ void taylor_interp_core(const Diff& D, const Emit& em
     }
   }
 
+}
+
+// Taylor coefficients (units of the fine spacing, the centre value c000
+// included) of the coarse centre (cl, a, b), evaluated at its children.
+template <int M, typename T, typename Diff, typename Emit>
+__device__ __forceinline__ void taylor_interp_core(const Diff& D, const Emit& emit, const T* __restrict__ wt,
+                                                   int k, int p, int a, int b, T c000, int cl = -1,
+                                                   int kk = 3) {
+  T C[M + 1][M + 1][M + 1];
+  taylor_interp_coeffs<M, T>(D, wt, k, p, a, b, c000, cl, C);
   taylor_children<M, T>(C, emit, kk < k ? kk : k);
 }
 
