@@ -607,6 +607,21 @@ def other_workloads(B, wl, stream):
     del items, coarse, fine, co
     torch.cuda.empty_cache()
     out["adjoint"] = adjoint_leg(B, wl, stream, 4096)
+    # diagonal (edge and vertex) ghost volumes of 256 hanging faces: every
+    # fine face array's ghost half widened by k on each tangential side
+    items, coarse, fine = wl.uniform_batch(n_faces=256, U=U, order=3, config_index=5, device="cuda")
+    plan = B.Plan(items, U, coarse.numel(), fine.numel(), B.PREC_FIXED)
+    diag = torch.empty(plan.diagonal_elems, dtype=torch.float64, device="cuda")
+    plan.interpolate_diagonal(coarse, diag)  # builds the tile table
+    t = time_kernel(lambda: plan.interpolate_diagonal(coarse, diag), 5, stream)
+    vols = plan.diagonal_elems // U
+    out["diagonal_halos"] = {"workload": "256 hanging faces, p=9, k=3, U=59, Taylor-3: widened ghost boxes "
+                                         "(p + 2k)^2 x k per fine face array, float64",
+                             "ms_per_call": t, "value": vols * U / (t * 1e-3), "unit": "volume-unknowns/s",
+                             "bytes_written": plan.diagonal_elems * 8}
+    plan.close()
+    del items, coarse, fine, diag
+    torch.cuda.empty_cache()
     return out
 
 
