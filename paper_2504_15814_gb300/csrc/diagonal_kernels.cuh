@@ -11,9 +11,8 @@
 // then exceeding one fine spacing) with that centre's derivative stencils and
 // Taylor's formula, or by the d-linear tensor product with linear
 // extrapolation past the edge.  Inside the subface the values equal the
-// ordinary interpolation.  Float64 arithmetic; one thread per (volume,
-// unknown), derivatives recomputed per volume (the widened boxes are small
-// next to the face arrays).
+// ordinary interpolation.  Float64 arithmetic; one thread per (coarse
+// centre, unknown) of each widened box.
 #pragma once
 #include "transfer_kernels.cuh"
 
@@ -52,10 +51,43 @@ __device__ __forceinline__ double dlinear_at(const Src& S, int k, int p, int a, 
   return lerp_at(A[0], A[1], A[2], blo, bhi, e1);
 }
 
+// Evaluate the Taylor-m polynomial with coefficients C (fine units) at
+// integer offsets (en, e0, e1).
+template <int M>
+__device__ __forceinline__ double taylor_at(const double (&C)[M + 1][M + 1][M + 1], int en, int e0, int e1) {
+  double v = 0.0, xn = 1.0;
+#pragma unroll
+  for (int x = 0; x <= M; ++x) {
+    double x1p = 1.0;
+#pragma unroll
+    for (int y = 0; x + y <= M; ++y) {
+      double x2p = 1.0;
+#pragma unroll
+      for (int z = 0; x + y + z <= M; ++z) {
+        v = fma(C[x][y][z], xn * x1p * x2p, v);
+        x2p *= (double)e1;
+      }
+      x1p *= (double)e0;
+    }
+    xn *= (double)en;
+  }
+  return v;
+}
+
+// Fine global indices [lo, hi] along one tangential axis whose nearest coarse
+// centre is a, within the widened box [box_lo, box_hi] (past the face's edges
+// the edge centres take every remaining index).
+__device__ __forceinline__ void centre_span(int a, int p, int box_lo, int box_hi, int& lo, int& hi) {
+  lo = a == 0 ? box_lo : max(3 * a, box_lo);
+  hi = a == p - 1 ? box_hi : min(3 * a + 2, box_hi);
+}
+
 // One tile = one fine face array (slot) of one item and a chunk of unknowns.
-// diag layout, from diag_off[item]: ((((slot k + g) W + q1 + k) W + q0 + k) U + u
-// with W = p + 2k, ghost layer g (0 next to the interface), tangential local
-// indices q0, q1 in [-k, p + k).
+// One thread per (coarse centre, unknown): the centre's Taylor coefficients
+// (or its d-linear neighbourhood) once, then every widened-box volume whose
+// nearest centre it is.  diag layout, from diag_off[item]:
+// ((((slot k + g) W + q1 + k) W + q0 + k) U + u with W = p + 2k, ghost layer g
+// (0 next to the interface), tangential local indices q0, q1 in [-k, p + k).
 __global__ void __launch_bounds__(256) interp_diagonal_kernel(const amr_transfer_item* __restrict__ items,
                                                               const AdjointTile* __restrict__ tiles, int U,
                                                               const int64_t* __restrict__ diag_off,
@@ -67,63 +99,42 @@ __global__ void __launch_bounds__(256) interp_diagonal_kernel(const amr_transfer
   const FaceFrame fr = face_frame(it.face, p, k);
   const int sub = it.subface < 0 ? t.slot : it.subface;
   const int s0 = sub % 3, s1 = sub / 3;
-  const int W = p + 2 * k, npos = k * W * W, nu = t.nu;
-  double* out = diag + diag_off[t.index] + (int64_t)t.slot * npos * U;
+  const int W = p + 2 * k, nu = t.nu;
+  double* out = diag + diag_off[t.index] + (int64_t)t.slot * k * W * W * U;
   const double* cb = coarse + it.coarse_offset;
-  for (int e = threadIdx.x; e < npos * nu; e += blockDim.x) {
-    const int u = t.u0 + e % nu, pos = e / nu;
-    const int q0 = pos % W - k, q1 = (pos / W) % W - k, g = pos / (W * W);
-    // fine global tangential indices; nearest coarse centre (clamped to the
-    // face) and the offsets from it, in fine spacings
-    const int g0 = s0 * p + q0, g1 = s1 * p + q1;
-    const int a = g0 < 0 ? 0 : min(g0 / 3, p - 1);
-    const int b = g1 < 0 ? 0 : min(g1 / 3, p - 1);
-    const int e0 = g0 - (3 * a + 1), e1 = g1 - (3 * b + 1), en = 1 - g;
+  // widened box in fine global indices, and the centres it reaches
+  const int lo0 = s0 * p - k, hi0 = s0 * p + p + k - 1, lo1 = s1 * p - k, hi1 = s1 * p + p + k - 1;
+  const int a_lo = lo0 < 0 ? 0 : min(lo0 / 3, p - 1), a_hi = min(hi0 / 3, p - 1);
+  const int b_lo = lo1 < 0 ? 0 : min(lo1 / 3, p - 1), b_hi = min(hi1 / 3, p - 1);
+  const int na = a_hi - a_lo + 1, nb = b_hi - b_lo + 1;
+  for (int e = threadIdx.x; e < na * nb * nu; e += blockDim.x) {
+    const int u = t.u0 + e % nu, c = e / nu;
+    const int a = a_lo + c % na, b = b_lo + c / na;
+    int g0a, g0b, g1a, g1b;
+    centre_span(a, p, lo0, hi0, g0a, g0b);
+    centre_span(b, p, lo1, hi1, g1a, g1b);
     auto S = [&](int j, int aa, int bb) -> double { return __ldg(cb + frame_vol(fr, j, aa, bb) * U + u); };
-    double v;
+    auto put = [&](int g, int g0, int g1, double v) {
+      out[((int64_t)(g * W + g1 - s1 * p + k) * W + (g0 - s0 * p + k)) * U + u] = v;
+    };
     if (m == 1) {
-      v = dlinear_at(S, k, p, a, b, en, e0, e1);
-    } else {
+      for (int g = 0; g < k; ++g)
+        for (int g1 = g1a; g1 <= g1b; ++g1)
+          for (int g0 = g0a; g0 <= g0b; ++g0)
+            put(g, g0, g1, dlinear_at(S, k, p, a, b, 1 - g, g0 - (3 * a + 1), g1 - (3 * b + 1)));
+    } else if (m == 3) {
       double C[4][4][4];
-      double xn = 1.0;
-      if (m == 3) {
-        double C3[4][4][4];
-        taylor_interp_coeffs<3, double>(S, c_wt_interp, k, p, a, b, S(-1, a, b), -1, C3);
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y)
-#pragma unroll
-            for (int z = 0; z < 4; ++z) C[x][y][z] = C3[x][y][z];
-      } else {
-        double C2[3][3][3];
-        taylor_interp_coeffs<2, double>(S, c_wt_interp, k, p, a, b, S(-1, a, b), -1, C2);
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y)
-#pragma unroll
-            for (int z = 0; z < 4; ++z) C[x][y][z] = (x < 3 && y < 3 && z < 3) ? C2[x][y][z] : 0.0;
-      }
-      // sum over |alpha| <= m of C_alpha en^x e0^y e1^z
-      v = 0.0;
-#pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        double x1p = 1.0;
-#pragma unroll
-        for (int y = 0; x + y < 4; ++y) {
-          double x2p = 1.0;
-#pragma unroll
-          for (int z = 0; x + y + z < 4; ++z) {
-            v = fma(C[x][y][z], xn * x1p * x2p, v);
-            x2p *= (double)e1;
-          }
-          x1p *= (double)e0;
-        }
-        xn *= (double)en;
-      }
+      taylor_interp_coeffs<3, double>(S, c_wt_interp, k, p, a, b, S(-1, a, b), -1, C);
+      for (int g = 0; g < k; ++g)
+        for (int g1 = g1a; g1 <= g1b; ++g1)
+          for (int g0 = g0a; g0 <= g0b; ++g0) put(g, g0, g1, taylor_at<3>(C, 1 - g, g0 - (3 * a + 1), g1 - (3 * b + 1)));
+    } else {
+      double C[3][3][3];
+      taylor_interp_coeffs<2, double>(S, c_wt_interp, k, p, a, b, S(-1, a, b), -1, C);
+      for (int g = 0; g < k; ++g)
+        for (int g1 = g1a; g1 <= g1b; ++g1)
+          for (int g0 = g0a; g0 <= g0b; ++g0) put(g, g0, g1, taylor_at<2>(C, 1 - g, g0 - (3 * a + 1), g1 - (3 * b + 1)));
     }
-    out[(int64_t)pos * U + u] = v;
   }
 }
 
