@@ -287,10 +287,12 @@ __global__ void __launch_bounds__(kAdjThreads)
 // ---------------------------------------------------------------------------
 // g_coarse = P^T g_fine, fixed point, for one group of items sharing a
 // coarse face array (finite-difference items, p a multiple of 3) and a chunk
-// of <= 32 unknowns.  One warp per coarse centre, lane = unknown.  Writes
-// every value of the group's coarse face array (zero where nothing reaches).
-// rn_lo / rn_hi: signed normal layers of the accumulator (the union of the
-// items' stencil regions).
+// of <= 32 unknowns, after adjoint_emax_kernel has left the grid exponents
+// in the array.  One warp per coarse centre, lane = unknown: the centre's
+// child gradients rounded onto the grid, reduced to moments and scattered
+// through the transposed stencils into the shared-memory accumulator (rows
+// rlo..rhi: the union of the items' normal stencil ranges); then every value
+// of the group's coarse face array is written (zero where nothing reaches).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kAdjThreads, 2)
     interp_adjoint_fixed_kernel(const amr_transfer_item* __restrict__ items, const AdjointTile* __restrict__ tiles,
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
   const int E = lane < nu ? (int)reinterpret_cast<const long long*>(g_coarse)[first.coarse_offset + t.u0 + lane] : 0;
   const bool finite = E < 2047;
   const int s = kAdjBits - (max(E, 62) - 1022);  // |g| < 2^(E - 1022) -> |n| < 2^44
-  // pass B: per item and coarse centre (one warp), the transposed operator
+  // per item and coarse centre (one warp), the transposed operator
   if (lane < nu) {
     for (int mi = m0; mi < m1; ++mi) {
       const amr_transfer_item it = items[group_items[mi]];
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
     }
   }
   __syncthreads();
-  // pass C: every value of the coarse face array (chunk of unknowns)
+  // every value of the coarse face array (chunk of unknowns)
   const uint32_t ovf_hi = finite ? 0x7ff00000u : 0x7ff80000u;
   const int sh = finite ? s : -4000;
   if (lane < nu) {
